@@ -182,3 +182,18 @@ def test_projector_approximates_analytic_phantom(ora):
         p_vox = ora.project(ora.Geometry(geom), truth)
         errs.append(np.linalg.norm(p_vox - p_ana) / np.linalg.norm(p_ana))
     assert errs[1] < 0.05 and errs[1] < 0.6 * errs[0], errs
+
+
+def test_ray_in_outer_face_half_open(ora):
+    """A ray lying exactly in the volume's lower y face is inside (row 0); one
+    lying in the upper y face is outside (projection 0)."""
+    for cy, expect_row in ((2.0, 0), (-2.0, None)):
+        geom = synth.make_geometry(nx=6, ny=4, nz=3, dx=1.0, cy=cy, nu=5, nv=3, du=1.0, sad=30, sdd=45,
+                                   n_phases=2, views_per_phase=1, angles=[0.0, 0.5])
+        G = ora.Geometry(geom)
+        f = synth.uniform(G.vol_shape, 9).astype(np.float64)
+        p = ora.project(G, f)
+        if expect_row is None:
+            assert p[0, 1, 2] == 0.0
+        else:
+            assert p[0, 1, 2] == pytest.approx(f[0, 1, expect_row, :].sum(), rel=1e-13)

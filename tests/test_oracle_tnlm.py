@@ -275,3 +275,27 @@ def test_np2_both_terms_present(ora):
                     acc += w[0, 0, z, y, x, k] * v[1, Z, Y, X]
                 k += 1
     assert f[0, z, y, x] == pytest.approx((mu * g[0, z, y, x] + 2 * acc) / (2 + mu), rel=1e-13)
+
+
+def test_weight_directions_three_phases(ora):
+    """Phase 1 = phase 0 moved by +s, phase 2 = moved by -s: direction 0 of
+    phase 0 (toward i+1) is one-hot at +s, direction 1 (toward i-1) at -s."""
+    rng = np.random.default_rng(32)
+    base = rng.uniform(size=(10, 10, 10))
+    s = (1, 0, -2)  # (dz, dy, dx)
+    a = np.stack([base, np.roll(base, s, axis=(0, 1, 2)), np.roll(base, tuple(-t for t in s), axis=(0, 1, 2))])
+    w = ora.weights(a, 1, 2, 0.02)
+    kp = ((s[0] + 2) * 5 + (s[1] + 2)) * 5 + (s[2] + 2)
+    km = ((-s[0] + 2) * 5 + (-s[1] + 2)) * 5 + (-s[2] + 2)
+    assert w[0, 0, 4, 5, 5][kp] == pytest.approx(1.0, abs=1e-12)
+    assert w[0, 1, 4, 5, 5][km] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_apply_of_exported_weights_equals_sweep(ora):
+    shape = (3, 4, 5, 6)
+    a = synth.uniform(shape, 33).astype(np.float64)
+    v = synth.uniform(shape, 34).astype(np.float64)
+    g = synth.uniform(shape, 35).astype(np.float64)
+    d, M, h, mu = 1, 1, 0.35, 0.9
+    np.testing.assert_allclose(ora.gj_apply(ora.weights(a, d, M, h), M, v, g, mu),
+                               ora.gj_sweep(a, v, g, d, M, h, mu), rtol=1e-13)
