@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the TNLM 4D-CBCT forward-backward-splitting hot path on GB300.
+
+Workload (the NCAT-shaped reconstruction): 10 phases, 256 x 256 x 64 volume
+at 2 mm, 36 views per phase (360 over one rotation, phase-interleaved) on a
+512 x 384 detector at 0.78 mm, SAD 1000 / SDD 1500 mm, patch 3^3 (d = 1),
+search window 7^3 (M = 3), h = 0.02, mu = 1.  Inputs are synthetic: a seeded
+thorax phantom, analytic line integrals, Poisson noise at I0 = 5e4.
+
+One step = one FBS iteration of TNLM-R through tnlm_reconstruct: forward
+projection + residual of every phase, voxel-driven transpose + gradient
+step, fused weights + Gauss-Jacobi sweep + positivity.  Inputs (y: 283 MB,
+f: 168 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank reconstructs its own problem (independent 4D
+reconstructions, weak scaling, no collective on the data path); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FBS iterations/s and TNLM voxel-updates/s on 1 GB300; % HBM roofline vs FP32"
+UNIT = "FBS iterations/s"
+WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views/phase on 512x384 @ 0.78 mm, "
+            "SAD 1000 / SDD 1500, patch 3^3, window 7^3, h 0.02, mu 1")
+
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# each kernel on this workload, with the SHA-256 of the kernel source it was
+# measured on; a changed source invalidates the figure (reported as null).
+NCU_TRAFFIC = {}
+
+
+def _src_sha(fname: str) -> str:
+    p = os.path.join(ROOT, "paper_1201_2450_gb300", "csrc", fname)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+KERNEL_SRC = {"k_forward": "projector.cu", "k_backproject": "projector.cu", "k_sweep": "tnlm_sweep.cu"}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "_source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work and bytes per launch ("Roofline")
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(cfg, n_views_total):
+    npz = cfg.n_phases * cfg.vol[0] * cfg.vol[1] * cfg.vol[2]
+    npix = n_views_total * cfg.det[0] * cfg.det[1]
+    return {
+        "k_forward": 4 * npz + 4 * npix + 4 * npix,     # read f, read y, write scaled residual
+        "k_backproject": 4 * npix + 4 * npz + 4 * npz,  # read residual, read f, write g
+        "k_sweep": 4 * npz + 4 * npz,                   # read g (weights, values, fidelity), write f
+    }
+
+
+def sweep_pairs(cfg):
+    """Pair evaluations of one sweep: every voxel, both directions, every
+    window offset that stays inside the volume."""
+    nx, ny, nz = cfg.vol
+    M = cfg.M
+
+    def valid(n):
+        return sum(min(n - 1, i + M) - max(0, i - M) + 1 for i in range(n))
+
+    return 2 * cfg.n_phases * valid(nx) * valid(ny) * valid(nz)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import paper_1201_2450_gb300 as tnlm
+    from paper_1201_2450_gb300 import synth
+
+    torch.cuda.set_device(local)
+    tnlm.build()
+    cfg = synth.C2
+    pb = synth.recon_problem(cfg, device="cuda")  # same seeded problem on every rank
+    geom = tnlm.Geometry(pb.geom)
+    y = pb.y.contiguous()
+    x0 = torch.from_numpy(synth.uniform(geom.vol_shape, 2024)).cuda()
+    L = tnlm.tnlm_operator_norm(geom, x0, 20)
+    tau = 1.0 / L
+    params = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=1, n_inner=1, clip_nonneg=1)
+    f = torch.zeros(geom.vol_shape, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        tnlm.tnlm_reconstruct(geom, y, f, params)
+    torch.cuda.synchronize()
+
+    geom.set_stage_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tnlm.tnlm_reconstruct(geom, y, f, params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, stage_n = geom.stage_timing()
+    geom.set_stage_timing(False)
+    ms_max = max_over_ranks(ms_total, world)
+    value = args.steps * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers
+    y_host = y.cpu().pin_memory()
+    f_host = torch.zeros(geom.vol_shape).pin_memory()
+    y_dev = torch.empty_like(y)
+    f_dev = torch.empty_like(f)
+    tnlm.reconstruct_host(geom, y_host, f_host, params, y_dev, f_dev)  # warm
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    e_steps = max(1, min(args.steps, 5))
+    for _ in range(e_steps):
+        h2d, d2h = tnlm.reconstruct_host(geom, y_host, f_host, params, y_dev, f_dev)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = e_steps * world / e2e_s
+
+    peaks = measured_peaks()
+    names = ["k_forward", "k_backproject", "k_sweep"]
+    per_launch_ms = {n: stage_ms[k] / max(stage_n[k], 1) for k, n in enumerate(names)}
+    abytes = algorithmic_bytes(cfg, geom.proj_shape[0])
+    hbm = {}
+    for n in names:
+        gbs = abytes[n] / (per_launch_ms[n] / 1e3) / 1e9
+        hbm[n] = {"ms_per_launch": round(per_launch_ms[n], 4), "algorithmic_bytes": abytes[n],
+                  "achieved_gbs": round(gbs, 2), "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 5)}
+    dom = max(names, key=lambda n: per_launch_ms[n])
+    traffic = None
+    t = NCU_TRAFFIC.get(dom)
+    if t and t.get("source_sha") == _src_sha(KERNEL_SRC[dom]):
+        traffic = t["bytes_per_launch"]
+    dom_gbs = abytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(dom_gbs, 2), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(dom_gbs / peaks["hbm_gbs"], 5), "traffic": traffic,
+                "peak_source": peaks["_source"] + " (burst copy)"}
+    nvox_upd = cfg.n_phases * cfg.vol[0] * cfg.vol[1] * cfg.vol[2]
+    sweep_s = per_launch_ms["k_sweep"] / 1e3
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "phases": cfg.n_phases, "volume": list(cfg.vol), "voxel_mm": cfg.voxel_mm,
+                   "views_per_phase": cfg.views_per_phase, "detector": list(cfg.det), "pixel_mm": cfg.pixel_mm,
+                   "d": cfg.d, "M": cfg.M, "h": cfg.h, "mu": cfg.mu, "tau": tau, "n_inner": 1,
+                   "step": "one FBS iteration (projection+residual, transpose+gradient step, weights+Gauss-Jacobi+clip)",
+                   "l2": "inputs larger than L2 (y 283 MB, f 168 MB), no flush",
+                   "parallelism": f"replicas x{world} (independent reconstructions)"},
+        "tnlm_voxel_updates_per_s": round(nvox_upd / sweep_s, 1),
+        "tnlm_pair_evals_per_s": round(sweep_pairs(cfg) / sweep_s, 1),
+        "stage_ms_per_launch": {n: round(per_launch_ms[n], 4) for n in names},
+        "hbm": hbm,
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": int(sum(stage_n)),
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(cfg, pb)
+    return line
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_baseline_sample(cfg, pb=None) -> dict:
+    """Time the FP64 oracle as it stands on a bounded sample of one FBS
+    iteration of the workload and extrapolate to iterations/s:
+    projection and transpose of 2 views (x 360 views), one sweep on a
+    3-phase 256 x 256 x 4 slab (x voxel-updates of 10 x 256^2 x 64)."""
+    import oracle
+    from paper_1201_2450_gb300 import synth
+
+    oracle.build()
+    geom = cfg.geometry() if pb is None else pb.geom
+    truth = (pb.truth.cpu() if pb is not None else synth.rasterize(geom, synth._objects(cfg))).numpy()
+    nview = 2
+    sub = dict(geom)
+    sub["nviews"] = np.array([nview], np.int32)
+    sub["angles"] = np.asarray(geom["angles"][:nview])
+    G1 = oracle.Geometry(sub)
+    vol1 = truth[:1].astype(np.float64)
+    t0 = time.perf_counter()
+    p = oracle.project(G1, vol1)
+    t1 = time.perf_counter()
+    oracle.backproject(G1, p)
+    t2 = time.perf_counter()
+    slab = truth[:3, 30:34].astype(np.float64)
+    oracle.gj_sweep(slab, slab, slab, cfg.d, cfg.M, cfg.h, cfg.mu, 1)
+    t3 = time.perf_counter()
+    n_views = int(np.sum(geom["nviews"]))
+    per_iter = (t1 - t0) / nview * n_views + (t2 - t1) / nview * n_views + \
+        (t3 - t2) * (cfg.n_phases * cfg.vol[2]) / (3 * 4)
+    return {"value": round(1.0 / per_iter, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: P and P^T of {nview} views (x{n_views}), one sweep on 3 phases x 256x256x4 "
+                      f"(x{cfg.n_phases * cfg.vol[2] / 12:.1f}); {t3 - t0:.1f} s measured, "
+                      f"{per_iter:.1f} s per iteration extrapolated"}
+
+
+def run_reference(args, rank, world):
+    from paper_1201_2450_gb300 import synth
+    if rank != 0:
+        return None
+    cfg = synth.C2
+    for _ in range(args.warmup):
+        cpu_baseline_sample(cfg)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline_sample(cfg))
+    wall = time.perf_counter() - t0
+    value = statistics.median(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (bounded sample, extrapolated)"},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * tnlm.h -- C ABI of libtnlm.so, the GB300 (sm_103a) implementation of the
+ * temporal non-local means (TNLM) 4D cone-beam CT method: the forward-
+ * backward-splitting reconstruction (TNLM-R) and the enhancement (TNLM-E)
+ * of Jia, Tian, Lou, Sonke and Jiang (arXiv:1201.2450).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Volumes are float32 [n_phases][nz][ny][nx] (x fastest), contiguous.
+ *  - Projections are float32 [sum of n_views][nv][nu] (u fastest),
+ *    contiguous; the views of phase 0 come first, then phase 1, ...
+ *  - Every array argument is a DEVICE pointer owned by the caller, on the
+ *    device that was current when the geometry was created (or, for the
+ *    geometry-free calls, the current device).  The library never frees it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls only enqueue work: results are ready once the stream is
+ *    synchronised.  The returned status covers argument validation and
+ *    launch errors; an error raised while a kernel runs surfaces at the
+ *    caller's next synchronisation (or inside calls that return host data).
+ *  - No exception crosses the ABI.  On failure, tnlm_last_error() returns a
+ *    thread-local message.
+ *  - Scan geometry (Sec. 2.5 describes the circular cone-beam protocol):
+ *    rotation about z; source at SAD (cos t, sin t, 0); flat detector centred
+ *    at (SAD - SDD)(cos t, sin t, 0) with axes u = (-sin t, cos t, 0) and
+ *    v = (0, 0, 1); pixel (iu, iv) centre at u = (iu - (nu-1)/2) du + u_off,
+ *    v = (iv - (nv-1)/2) dv + v_off; voxel (ix,iy,iz) is the half-open cell
+ *    centred at ((ix - (nx-1)/2) dx + cx, ...).  Lengths in mm, attenuation
+ *    in 1/mm, projections are dimensionless line integrals.
+ */
+#ifndef TNLM_H
+#define TNLM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNLM_OK = 0,
+    TNLM_ERR_ARG = 1,             /* invalid argument (null pointer, bad size, N_p < 2, h <= 0, ...) */
+    TNLM_ERR_CUDA = 2,            /* a CUDA runtime call or kernel launch failed */
+    TNLM_ERR_OOM = 3,             /* device memory for the library's workspace could not be allocated */
+    TNLM_ERR_TIMEOUT = 4,         /* reserved for bounded device-side waits */
+    TNLM_ERR_NOT_IMPLEMENTED = 5  /* parameter combination without a kernel */
+} tnlm_status;
+
+/* Opaque scan-geometry handle; owns the per-view tables on the device and
+ * the workspace of tnlm_reconstruct / tnlm_operator_norm.  A handle may be
+ * used by one host thread at a time. */
+typedef struct tnlm_geometry tnlm_geometry;
+
+/* Problem statement of Eq. 1: N_p phase images f_i, the projections y_i of
+ * each phase bin (uneven counts allowed, Sec. 2.5) and the cone-beam
+ * geometry of Sec. 2.5. */
+typedef struct {
+    int nx, ny, nz;          /* volume size in voxels (each >= 1) */
+    double dx, dy, dz;       /* voxel size, mm (> 0) */
+    double cx, cy, cz;       /* volume centre offset from the isocentre, mm */
+    int nu, nv;              /* detector size in pixels (each >= 1) */
+    double du, dv;           /* pixel pitch, mm (> 0) */
+    double u_off, v_off;     /* detector centre offset along u and v, mm */
+    double sad, sdd;         /* source-isocentre and source-detector distances, mm (sdd > sad > 0) */
+    int n_phases;            /* N_p >= 2 */
+    const int *n_views;      /* host array [n_phases], each >= 1 */
+    const double *angles_rad;/* host array [sum n_views], phase-major view angles */
+} tnlm_geometry_desc;
+
+/* Parameters of TNLM-R / TNLM-E (Sec. 2.3).  d: patch radius, the patch is
+ * the (2d+1)^3 cube of Eq. 3; M: search-window radius, the window is the
+ * (2M+1)^3 cube of Sec. 2.4; h: filtering parameter of Eq. 3 (> 0); mu:
+ * fidelity weight of Eq. 1 / Eq. 4 (> 0); tau: step of the (P1) gradient
+ * step g <- g - tau P^T (P g - y) (tau <= 1/||P||^2 guarantees descent). */
+typedef struct {
+    int d;            /* 0 <= d <= 3 */
+    int M;            /* 0 <= M <= 4 */
+    float h;
+    float mu;
+    float tau;        /* TNLM-R only */
+    int n_outer;      /* TNLM-R: FBS iterations; TNLM-E: Gauss-Jacobi sweeps (>= 0) */
+    int n_inner;      /* TNLM-R: gradient steps per (P1) (>= 1) */
+    int clip_nonneg;  /* 1: positivity correction f <- max(f, 0) after Eq. 8 (TNLM-R step 4) */
+    int gj_start;     /* TNLM-R: 0 = Eq. 8 iterate starts at g^(k) (default), 1 = at f^(k-1) */
+} tnlm_params;
+
+/* Create a geometry handle from `desc` (copied; the desc arrays may be freed
+ * afterwards).  Uploads the per-view tables to the current device.
+ * Returns TNLM_ERR_ARG for an invalid description. */
+tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry **out);
+
+/* Release a handle and its device memory (NULL is ignored).  Synchronises
+ * the device first so no queued call still uses the workspace. */
+void tnlm_destroy_geometry(tnlm_geometry *geom);
+
+/* proj = P vol for every phase: the ray-driven exact radiological path
+ * (Siddon, the paper's ref. 40, used for the projections of Sec. 2.5) of
+ * each source->pixel-centre segment through the voxel cells of that view's
+ * phase image (the operator P_i of Eq. 1).  vol: [N_p][nz][ny][nx]; proj:
+ * [sum n_views][nv][nu]; they must not overlap. */
+tnlm_status tnlm_project(const tnlm_geometry *geom, const float *vol, float *proj, void *stream);
+
+/* vol = beta * vol + alpha * P^T proj: the exact transpose of tnlm_project,
+ * evaluated voxel-driven (each voxel gathers over the pixels whose rays cross
+ * it), as used by the (P1) gradient of Eq. 5.  vol may hold garbage when
+ * beta == 0. */
+tnlm_status tnlm_backproject(const tnlm_geometry *geom, const float *proj, float *vol, float alpha, float beta,
+                             void *stream);
+
+/* Normalised TNLM weights of Eq. 9 (Eq. 3 with the weight-source images
+ * wsrc), exported for inspection: for every phase i, direction k (0: toward
+ * phase i+1, 1: toward phase i-1, periodic in phase per Sec. 2.1), voxel x
+ * and window offset (dz slowest, dx fastest),
+ *   w = exp(-||p(x) - p'(x+delta)||^2 / 2h^2) / Z,
+ * normalised over the valid offsets of the (2M+1)^3 window; patches clamp to
+ * the volume edge; offsets leaving the volume get weight 0.
+ * w_out: [N_p][2][nz][ny][nx][(2M+1)^3]; w_out_len is its length in floats
+ * and must be at least that size (TNLM_ERR_ARG otherwise). */
+tnlm_status tnlm_weights(int nx, int ny, int nz, int n_phases, const float *wsrc, int d, int M, float h,
+                         float *w_out, size_t w_out_len, void *stream);
+
+/* One Gauss-Jacobi sweep of Eq. 8 with the weights of Eq. 9 computed on the
+ * fly from wsrc:
+ *   f_out_i = mu/(2+mu) g_i + 1/(2+mu) (W_{i,i+1} vals_{i+1} + W_{i,i-1} vals_{i-1}),
+ * followed by f_out <- max(f_out, 0) when clip != 0.  f_out must not overlap
+ * wsrc, vals or g (Jacobi: every phase reads the old values). */
+tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float *wsrc, const float *vals,
+                              const float *g, float *f_out, int d, int M, float h, float mu, int clip,
+                              void *stream);
+
+/* TNLM-R (Sec. 2.3): f holds f^(0) on entry and f^(n_outer) on exit.  Each
+ * FBS iteration k: (P1) n_inner gradient steps g <- g - tau P^T (P g - y)
+ * from g = f^(k-1); weights from g^(k) (Eq. 9); one Eq. 8 sweep; positivity
+ * when clip_nonneg.  y: [sum n_views][nv][nu].  report (HOST pointer,
+ * nullable) receives ||P g - y||^2 (FP64) before every gradient step,
+ * [n_outer][n_inner]; when it is given the call synchronises `stream`.
+ * The first call allocates the handle's workspace (cudaMalloc, about
+ * sum(n_views) nu nv + N_p nx ny nz floats); make it before any capture. */
+tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, const tnlm_params *params,
+                             double *report, void *stream);
+
+/* TNLM-E (Sec. 2.3): f^(0) = g, then params->n_outer sweeps of (weights of
+ * Eq. 9 from f^(k), Eq. 8 with fidelity image g).  Uses params d, M, h, mu,
+ * n_outer and clip_nonneg.  g and f must not overlap.  Allocates one
+ * N_p nx ny nz float buffer stream-ordered (cudaMallocAsync) per call. */
+tnlm_status tnlm_enhance(int nx, int ny, int nz, int n_phases, const float *g, float *f, const tnlm_params *params,
+                         void *stream);
+
+/* Estimate L = ||P||_2^2 (so tau = 1/L for the (P1) step) by n_iter power
+ * iterations on P^T P from the start image x ([N_p][nz][ny][nx], device,
+ * overwritten).  *L_out (host) receives the Rayleigh quotient ||P x||^2 of
+ * the last normalised iterate, a lower bound of L.  Synchronises `stream`. */
+tnlm_status tnlm_operator_norm(tnlm_geometry *geom, float *x, int n_iter, double *L_out, void *stream);
+
+/* Per-stage timing of tnlm_reconstruct (instrumentation, off by default).
+ * When enabled, every tnlm_reconstruct call records CUDA events around the
+ * projector (stage 0), back-projector (1) and TNLM sweep (2) launches on its
+ * stream and synchronises at its end; tnlm_get_stage_timing returns the
+ * accumulated milliseconds and launch counts since the last enable. */
+tnlm_status tnlm_set_stage_timing(tnlm_geometry *geom, int enable);
+tnlm_status tnlm_get_stage_timing(const tnlm_geometry *geom, double ms[3], long long launches[3]);
+
+const char *tnlm_status_string(tnlm_status status);
+const char *tnlm_last_error(void);
+int tnlm_version(void); /* major * 10000 + minor * 100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNLM_H */

@@ -1,0 +1,296 @@
+"""GB300-native temporal non-local means (TNLM) 4D cone-beam CT.
+
+Thin ctypes binding of ``libtnlm.so`` (see ``include/tnlm.h``): the functions
+below carry the C-ABI names and only marshal arguments -- every arithmetic
+step runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.  If the library has not been built, every call raises; there is no
+CPU fallback.
+
+    import paper_1201_2450_gb300 as tnlm
+    tnlm.build()                                  # nvcc, sm_103a, in-tree
+    geom = tnlm.tnlm_create_geometry(desc)        # desc: dict (see synth.make_geometry)
+    proj = tnlm.tnlm_project(geom, vol)           # vol: cuda float32 [Np, nz, ny, nx]
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from ._build import LIB as _LIB_PATH
+from ._build import build
+
+__all__ = [
+    "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
+    "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_operator_norm",
+    "reconstruct_host", "library_path",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TnlmError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        self.status = status
+        super().__init__(f"{func} failed with status {status} ({_STATUS.get(status, '?')}): {detail}")
+
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "timeout",
+           5: "not implemented"}
+
+
+class _Desc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+        ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double),
+        ("nu", C.c_int), ("nv", C.c_int),
+        ("du", C.c_double), ("dv", C.c_double),
+        ("u_off", C.c_double), ("v_off", C.c_double),
+        ("sad", C.c_double), ("sdd", C.c_double),
+        ("n_phases", C.c_int),
+        ("n_views", C.POINTER(C.c_int)),
+        ("angles_rad", C.POINTER(C.c_double)),
+    ]
+
+
+class _Params(C.Structure):
+    _fields_ = [("d", C.c_int), ("M", C.c_int), ("h", C.c_float), ("mu", C.c_float), ("tau", C.c_float),
+                ("n_outer", C.c_int), ("n_inner", C.c_int), ("clip_nonneg", C.c_int), ("gj_start", C.c_int)]
+
+
+@dataclass
+class Params:
+    """TNLM-R / TNLM-E parameters (mirror of ``tnlm_params``)."""
+    d: int = 1
+    M: int = 2
+    h: float = 0.02
+    mu: float = 1.0
+    tau: float = 0.0
+    n_outer: int = 1
+    n_inner: int = 1
+    clip_nonneg: int = 1
+    gj_start: int = 0
+
+    def _c(self) -> _Params:
+        return _Params(self.d, self.M, self.h, self.mu, self.tau, self.n_outer, self.n_inner, self.clip_nonneg,
+                       self.gj_start)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_1201_2450_gb300.build() "
+                               "(this package has no CPU fallback)")
+        lib = C.CDLL(_LIB_PATH)
+        vp, i, f, sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
+        sig = {
+            "tnlm_create_geometry": (i, [C.POINTER(_Desc), C.POINTER(vp)]),
+            "tnlm_destroy_geometry": (None, [vp]),
+            "tnlm_project": (i, [vp, vp, vp, vp]),
+            "tnlm_backproject": (i, [vp, vp, vp, f, f, vp]),
+            "tnlm_weights": (i, [i, i, i, i, vp, i, i, f, vp, sz, vp]),
+            "tnlm_gauss_jacobi": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
+            "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
+            "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
+            "tnlm_set_stage_timing": (i, [vp, i]),
+            "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+            "tnlm_status_string": (C.c_char_p, [i]),
+            "tnlm_last_error": (C.c_char_p, []),
+            "tnlm_version": (i, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, func: str):
+    if status != 0:
+        raise TnlmError(status, func, _load().tnlm_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev(t: torch.Tensor, name: str, device: torch.device | None = None, shape=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+class Geometry:
+    """Owns a ``tnlm_geometry`` handle created on the current CUDA device."""
+
+    def __init__(self, desc: dict):
+        lib = _load()
+        self.desc = dict(desc)
+        self._nviews = np.ascontiguousarray(np.asarray(desc["nviews"], dtype=np.int32))
+        self._angles = np.ascontiguousarray(np.asarray(desc["angles"], dtype=np.float64))
+        d = _Desc()
+        for k in ("nx", "ny", "nz", "nu", "nv"):
+            setattr(d, k, int(desc[k]))
+        for k in ("dx", "dy", "dz", "cx", "cy", "cz", "du", "dv", "u_off", "v_off", "sad", "sdd"):
+            setattr(d, k, float(desc.get(k, 0.0)))
+        d.n_phases = int(self._nviews.size)
+        d.n_views = self._nviews.ctypes.data_as(C.POINTER(C.c_int))
+        d.angles_rad = self._angles.ctypes.data_as(C.POINTER(C.c_double))
+        if self._angles.size != int(self._nviews.sum()):
+            raise ValueError("angles must hold sum(nviews) entries")
+        h = C.c_void_p()
+        self._h = None
+        _check(lib.tnlm_create_geometry(C.byref(d), C.byref(h)), "tnlm_create_geometry")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.np = d.n_phases
+        self.vol_shape = (d.n_phases, d.nz, d.ny, d.nx)
+        self.proj_shape = (int(self._nviews.sum()), d.nv, d.nu)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _load().tnlm_destroy_geometry(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stage_timing(self, enable: bool):
+        _check(_load().tnlm_set_stage_timing(self._h, int(enable)), "tnlm_set_stage_timing")
+
+    def stage_timing(self):
+        ms = (C.c_double * 3)()
+        n = (C.c_longlong * 3)()
+        _check(_load().tnlm_get_stage_timing(self._h, ms, n), "tnlm_get_stage_timing")
+        return list(ms), list(n)
+
+
+def tnlm_create_geometry(desc: dict) -> Geometry:
+    return Geometry(desc)
+
+
+def tnlm_project(geom: Geometry, vol: torch.Tensor, proj: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """proj = P vol (exact radiological path, all phases)."""
+    if proj is None:
+        proj = torch.empty(geom.proj_shape, dtype=torch.float32, device=geom.device)
+    _check(_load().tnlm_project(geom.handle, _dev(vol, "vol", geom.device, geom.vol_shape),
+                                _dev(proj, "proj", geom.device, geom.proj_shape), _stream(stream)), "tnlm_project")
+    return proj
+
+
+def tnlm_backproject(geom: Geometry, proj: torch.Tensor, vol: torch.Tensor | None = None, alpha: float = 1.0,
+                     beta: float = 0.0, stream=None) -> torch.Tensor:
+    """vol = beta vol + alpha P^T proj."""
+    if vol is None:
+        vol = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+        beta = 0.0
+    _check(_load().tnlm_backproject(geom.handle, _dev(proj, "proj", geom.device, geom.proj_shape),
+                                    _dev(vol, "vol", geom.device, geom.vol_shape), alpha, beta, _stream(stream)),
+           "tnlm_backproject")
+    return vol
+
+
+def tnlm_weights(wsrc: torch.Tensor, d: int, M: int, h: float, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """Normalised Eq. 9 weights, [Np][2][nz][ny][nx][(2M+1)^3]."""
+    np_, nz, ny, nx = wsrc.shape
+    W = (2 * M + 1) ** 3
+    if out is None:
+        out = torch.empty((np_, 2, nz, ny, nx, W), dtype=torch.float32, device=wsrc.device)
+    _check(_load().tnlm_weights(nx, ny, nz, np_, _dev(wsrc, "wsrc"), d, M, h, _dev(out, "w_out", wsrc.device),
+                                out.numel(), _stream(stream)), "tnlm_weights")
+    return out
+
+
+def tnlm_gauss_jacobi(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d: int, M: int, h: float, mu: float,
+                      clip: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One Eq. 8 sweep with weights (Eq. 9) from wsrc."""
+    np_, nz, ny, nx = wsrc.shape
+    if out is None:
+        out = torch.empty_like(wsrc)
+    dev = wsrc.device
+    _check(_load().tnlm_gauss_jacobi(nx, ny, nz, np_, _dev(wsrc, "wsrc"), _dev(vals, "vals", dev, wsrc.shape),
+                                     _dev(g, "g", dev, wsrc.shape), _dev(out, "f_out", dev, wsrc.shape), d, M, h,
+                                     mu, int(clip), _stream(stream)), "tnlm_gauss_jacobi")
+    return out
+
+
+def tnlm_reconstruct(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: Params, report: bool = False,
+                     stream=None):
+    """TNLM-R in place on f; returns (f, report or None)."""
+    rep = np.zeros((params.n_outer, params.n_inner), np.float64) if report else None
+    p = params._c()
+    _check(_load().tnlm_reconstruct(geom.handle, _dev(y, "y", geom.device, geom.proj_shape),
+                                    _dev(f, "f", geom.device, geom.vol_shape), C.byref(p),
+                                    rep.ctypes.data if rep is not None else None, _stream(stream)),
+           "tnlm_reconstruct")
+    return f, rep
+
+
+def tnlm_enhance(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """TNLM-E: f^(0) = g, params.n_outer sweeps."""
+    np_, nz, ny, nx = g.shape
+    if out is None:
+        out = torch.empty_like(g)
+    p = params._c()
+    _check(_load().tnlm_enhance(nx, ny, nz, np_, _dev(g, "g"), _dev(out, "f", g.device, g.shape), C.byref(p),
+                                _stream(stream)), "tnlm_enhance")
+    return out
+
+
+def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:
+    """||P||^2 estimate (power iteration); x is overwritten."""
+    L = C.c_double()
+    _check(_load().tnlm_operator_norm(geom.handle, _dev(x, "x", geom.device, geom.vol_shape), n_iter, C.byref(L),
+                                      _stream(stream)), "tnlm_operator_norm")
+    return L.value
+
+
+def reconstruct_host(geom: Geometry, y_host: torch.Tensor, f_host: torch.Tensor, params: Params,
+                     y_dev: torch.Tensor | None = None, f_dev: torch.Tensor | None = None, stream=None):
+    """TNLM-R on host (pinned) buffers: copy y and f to the device, run
+    tnlm_reconstruct, copy f back into f_host.  Returns the H2D and D2H byte
+    counts."""
+    if y_dev is None:
+        y_dev = torch.empty(geom.proj_shape, dtype=torch.float32, device=geom.device)
+    if f_dev is None:
+        f_dev = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+    y_dev.copy_(y_host, non_blocking=True)
+    f_dev.copy_(f_host, non_blocking=True)
+    tnlm_reconstruct(geom, y_dev, f_dev, params, stream=stream)
+    f_host.copy_(f_dev, non_blocking=True)
+    return y_host.numel() * 4 + f_host.numel() * 4, f_host.numel() * 4

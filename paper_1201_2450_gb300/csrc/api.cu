@@ -1,0 +1,408 @@
+// C ABI of libtnlm.so: argument validation, the geometry handle, the host
+// loops of TNLM-R and TNLM-E (Sec. 2.3) and the power iteration.  Every
+// arithmetic step runs in the kernels of projector.cu, tnlm_sweep.cu and
+// reduce.cu; this file only orders launches on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tnlm_internal.cuh"
+
+namespace tnlm {
+
+static thread_local char g_last_error[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+static tnlm_status arg_error(const char *msg)
+{
+    set_error("%s", msg);
+    return TNLM_ERR_ARG;
+}
+
+static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+template <class T>
+static tnlm_status dev_alloc(T **p, size_t count)
+{
+    if (*p) return TNLM_OK;
+    if (cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes for the workspace failed", sizeof(T) * count);
+        return TNLM_ERR_OOM;
+    }
+    return TNLM_OK;
+}
+
+static tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars)
+{
+    const KGeom &kg = g->kg;
+    TNLM_TRY(dev_alloc(&g->d_r, (size_t)g->n_views_total * kg.npix));
+    TNLM_TRY(dev_alloc(&g->d_g, (size_t)kg.np * kg.nvox));
+    if (need_tmp) TNLM_TRY(dev_alloc(&g->d_tmp, (size_t)kg.np * kg.nvox));
+    if (!g->d_part) {
+        long long n = forward_blocks(kg, g->n_views_total);
+        if (n < sumsq_scratch_len()) n = sumsq_scratch_len();
+        TNLM_TRY(dev_alloc(&g->d_part, (size_t)n));
+        g->part_len = n;
+    }
+    if (n_scalars > g->scalars_len) {
+        if (g->d_scalars) cudaFree(g->d_scalars);
+        g->d_scalars = nullptr;
+        TNLM_TRY(dev_alloc(&g->d_scalars, (size_t)n_scalars));
+        g->scalars_len = n_scalars;
+    }
+    return TNLM_OK;
+}
+
+// Records CUDA events around the launches of one stage when timing is on.
+struct StageTimer {
+    tnlm_geometry *g;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> stage;
+    StageTimer(tnlm_geometry *g_, cudaStream_t s) : g(g_), st(s) {}
+    void begin(int s)
+    {
+        if (!g->timing) return;
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, st);
+        ev.push_back(a);
+        stage.push_back(s);
+    }
+    void end()
+    {
+        if (!g->timing) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, st);
+        ev.push_back(b);
+    }
+    tnlm_status finish()
+    {
+        if (!g->timing) return TNLM_OK;
+        TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+        for (size_t k = 0; k + 1 < ev.size(); k += 2) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            g->stage_ms[stage[k / 2]] += ms;
+            g->stage_launches[stage[k / 2]] += 1;
+        }
+        for (auto e : ev) cudaEventDestroy(e);
+        ev.clear();
+        return TNLM_OK;
+    }
+    ~StageTimer()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace tnlm
+
+using namespace tnlm;
+
+extern "C" {
+
+const char *tnlm_status_string(tnlm_status s)
+{
+    switch (s) {
+    case TNLM_OK: return "ok";
+    case TNLM_ERR_ARG: return "invalid argument";
+    case TNLM_ERR_CUDA: return "CUDA error";
+    case TNLM_ERR_OOM: return "out of device memory";
+    case TNLM_ERR_TIMEOUT: return "device wait timed out";
+    case TNLM_ERR_NOT_IMPLEMENTED: return "not implemented";
+    }
+    return "unknown status";
+}
+
+const char *tnlm_last_error(void) { return g_last_error; }
+
+int tnlm_version(void) { return 10000; }
+
+tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry **out)
+{
+    if (!desc || !out) return arg_error("desc and out must not be NULL");
+    *out = nullptr;
+    const tnlm_geometry_desc &d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return arg_error("volume dimensions must be >= 1");
+    if ((long long)d.nx * d.ny * d.nz >= (1LL << 31)) return arg_error("a phase volume must hold fewer than 2^31 voxels");
+    if (!finite_pos(d.dx) || !finite_pos(d.dy) || !finite_pos(d.dz)) return arg_error("voxel sizes must be positive");
+    if (d.nu < 1 || d.nv < 1) return arg_error("detector dimensions must be >= 1");
+    if ((long long)d.nu * d.nv >= (1LL << 31)) return arg_error("a projection must hold fewer than 2^31 pixels");
+    if (d.nv > 6144) return arg_error("nv must not exceed 6144");
+    if (!finite_pos(d.du) || !finite_pos(d.dv)) return arg_error("pixel pitches must be positive");
+    if (!std::isfinite(d.u_off) || !std::isfinite(d.v_off) || !std::isfinite(d.cx) || !std::isfinite(d.cy) ||
+        !std::isfinite(d.cz))
+        return arg_error("offsets must be finite");
+    if (!finite_pos(d.sad) || !finite_pos(d.sdd) || !(d.sdd > d.sad)) return arg_error("need 0 < sad < sdd");
+    if (d.n_phases < 2) return arg_error("n_phases must be >= 2 (N_p = 1 would compare a phase with itself)");
+    if (!d.n_views || !d.angles_rad) return arg_error("n_views and angles_rad must not be NULL");
+    long long total = 0;
+    for (int i = 0; i < d.n_phases; ++i) {
+        if (d.n_views[i] < 1) return arg_error("every phase needs at least one view");
+        total += d.n_views[i];
+    }
+    if (total > 65535) return arg_error("at most 65535 views in total");
+    for (long long k = 0; k < total; ++k)
+        if (!std::isfinite(d.angles_rad[k])) return arg_error("angles must be finite");
+    // the source must stay outside the volume: every xy corner of the volume closer to the axis than SAD
+    {
+        double rmax = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double x = d.cx + ((q & 1) ? 0.5 : -0.5) * d.nx * d.dx;
+            const double y = d.cy + ((q & 2) ? 0.5 : -0.5) * d.ny * d.dy;
+            rmax = std::fmax(rmax, std::sqrt(x * x + y * y));
+        }
+        if (!(rmax < d.sad)) return arg_error("the volume must lie inside the source circle (corner radius < sad)");
+    }
+
+    tnlm_geometry *g = new (std::nothrow) tnlm_geometry();
+    if (!g) return arg_error("host allocation failed");
+    cudaGetDevice(&g->device);
+    KGeom &k = g->kg;
+    k.nx = d.nx; k.ny = d.ny; k.nz = d.nz; k.np = d.n_phases;
+    k.dx = (float)d.dx; k.dy = (float)d.dy; k.dz = (float)d.dz;
+    k.inv_dx = (float)(1.0 / d.dx); k.inv_dy = (float)(1.0 / d.dy); k.inv_dz = (float)(1.0 / d.dz);
+    k.hx = (float)(0.5 * d.dx); k.hy = (float)(0.5 * d.dy); k.hz = (float)(0.5 * d.dz);
+    k.b0x = (float)(d.cx - 0.5 * d.nx * d.dx);
+    k.b0y = (float)(d.cy - 0.5 * d.ny * d.dy);
+    k.b0z = (float)(d.cz - 0.5 * d.nz * d.dz);
+    k.nu = d.nu; k.nv = d.nv;
+    k.du = (float)d.du; k.dv = (float)d.dv;
+    k.inv_du = (float)(1.0 / d.du); k.inv_dv = (float)(1.0 / d.dv);
+    k.u_off = (float)d.u_off; k.v_off = (float)d.v_off;
+    k.uc = (float)(0.5 * (d.nu - 1)); k.vc = (float)(0.5 * (d.nv - 1));
+    k.sad = (float)d.sad; k.sdd = (float)d.sdd; k.inv_sdd = (float)(1.0 / d.sdd);
+    k.alpha0 = (float)(d.sad / d.sdd);
+    k.nvox = (long long)d.nx * d.ny * d.nz;
+    k.npix = (long long)d.nu * d.nv;
+    g->n_views_total = (int)total;
+    g->n_views.assign(d.n_views, d.n_views + d.n_phases);
+    g->angles.assign(d.angles_rad, d.angles_rad + total);
+    g->view_off.resize(d.n_phases + 1);
+    g->view_off[0] = 0;
+    for (int i = 0; i < d.n_phases; ++i) g->view_off[i + 1] = g->view_off[i] + d.n_views[i];
+    std::vector<ViewGeom> hv(total);
+    for (int i = 0; i < d.n_phases; ++i)
+        for (int v = g->view_off[i]; v < g->view_off[i + 1]; ++v) {
+            hv[v].c = (float)std::cos(d.angles_rad[v]);
+            hv[v].s = (float)std::sin(d.angles_rad[v]);
+            hv[v].phase = i;
+            hv[v].pad = 0;
+        }
+    if (cudaMalloc(&g->d_views, sizeof(ViewGeom) * total) != cudaSuccess ||
+        cudaMalloc(&g->d_view_off, sizeof(int) * (d.n_phases + 1)) != cudaSuccess ||
+        cudaMemcpy(g->d_views, hv.data(), sizeof(ViewGeom) * total, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_view_off, g->view_off.data(), sizeof(int) * (d.n_phases + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        set_error("geometry upload failed: %s", cudaGetErrorString(e));
+        cudaFree(g->d_views);
+        cudaFree(g->d_view_off);
+        delete g;
+        return TNLM_ERR_CUDA;
+    }
+    *out = g;
+    return TNLM_OK;
+}
+
+void tnlm_destroy_geometry(tnlm_geometry *g)
+{
+    if (!g) return;
+    cudaDeviceSynchronize();
+    cudaFree(g->d_views);
+    cudaFree(g->d_view_off);
+    cudaFree(g->d_r);
+    cudaFree(g->d_g);
+    cudaFree(g->d_tmp);
+    cudaFree(g->d_part);
+    cudaFree(g->d_scalars);
+    delete g;
+}
+
+tnlm_status tnlm_project(const tnlm_geometry *g, const float *vol, float *proj, void *stream)
+{
+    if (!g || !vol || !proj) return arg_error("geometry, vol and proj must not be NULL");
+    return launch_forward(g->kg, g->d_views, g->n_views_total, vol, nullptr, proj, nullptr, 0, as_stream(stream));
+}
+
+tnlm_status tnlm_backproject(const tnlm_geometry *g, const float *proj, float *vol, float alpha, float beta,
+                             void *stream)
+{
+    if (!g || !vol || !proj) return arg_error("geometry, proj and vol must not be NULL");
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return arg_error("alpha and beta must be finite");
+    return launch_backproject(g->kg, g->d_views, g->d_view_off, proj, vol, vol, alpha, beta, false,
+                              as_stream(stream));
+}
+
+tnlm_status tnlm_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w_out,
+                         size_t w_out_len, void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, 1.0f));
+    if (!wsrc || !w_out) return arg_error("wsrc and w_out must not be NULL");
+    const size_t W = (size_t)(2 * M + 1) * (2 * M + 1) * (2 * M + 1);
+    const size_t nvox = (size_t)nx * ny * nz;
+    const size_t need = (size_t)np * 2 * nvox * W;
+    if (need / W / 2 / (size_t)np != nvox) return arg_error("weight array size overflows size_t");
+    if (w_out_len < need) {
+        set_error("w_out holds %zu floats but %zu are needed", w_out_len, need);
+        return TNLM_ERR_ARG;
+    }
+    return launch_weights(nx, ny, nz, np, wsrc, d, M, h, w_out, as_stream(stream));
+}
+
+tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
+                              float *f_out, int d, int M, float h, float mu, int clip, void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, mu));
+    if (!wsrc || !vals || !g || !f_out) return arg_error("wsrc, vals, g and f_out must not be NULL");
+    if (f_out == wsrc || f_out == vals || f_out == g) return arg_error("f_out must not alias wsrc, vals or g");
+    return launch_sweep(nx, ny, nz, np, wsrc, vals, g, f_out, d, M, h, mu, clip, as_stream(stream));
+}
+
+static tnlm_status check_params(const tnlm_params *p, bool recon)
+{
+    if (!p) return arg_error("params must not be NULL");
+    if (p->n_outer < 0) return arg_error("n_outer must be >= 0");
+    if (recon) {
+        if (p->n_inner < 1) return arg_error("n_inner must be >= 1");
+        if (!std::isfinite(p->tau)) return arg_error("tau must be finite");
+        if (p->gj_start != 0 && p->gj_start != 1) return arg_error("gj_start must be 0 or 1");
+    }
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, double *report,
+                             void *stream)
+{
+    if (!geo || !y || !f) return arg_error("geometry, y and f must not be NULL");
+    TNLM_TRY(check_params(p, true));
+    const KGeom &kg = geo->kg;
+    TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
+    const long long n_norms = (long long)p->n_outer * p->n_inner;
+    TNLM_TRY(ensure_workspace(geo, p->gj_start == 1, n_norms > 1 ? n_norms : 1));
+    cudaStream_t st = as_stream(stream);
+    StageTimer timer(geo, st);
+    const long long nblk = forward_blocks(kg, geo->n_views_total);
+    for (int k = 0; k < p->n_outer; ++k) {
+        // step 1: (P1) gradient steps from f^(k-1)
+        for (int t = 0; t < p->n_inner; ++t) {
+            const float *src = t == 0 ? f : geo->d_g;
+            timer.begin(0);
+            TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
+            timer.end();
+            if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
+            timer.begin(1);
+            TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, geo->d_g, -p->tau, 1.0f,
+                                        true, st));
+            timer.end();
+        }
+        // steps 2-4: weights from g^(k) fused into one Eq. 8 sweep, positivity
+        timer.begin(2);
+        if (p->gj_start == 0) {
+            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, geo->d_g, geo->d_g, f, p->d, p->M, p->h,
+                                  p->mu, p->clip_nonneg, st));
+        } else {
+            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, f, geo->d_g, geo->d_tmp, p->d, p->M, p->h,
+                                  p->mu, p->clip_nonneg, st));
+            TNLM_TRY_CUDA(cudaMemcpyAsync(f, geo->d_tmp, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+        }
+        timer.end();
+    }
+    if (report && n_norms > 0) {
+        TNLM_TRY_CUDA(cudaMemcpyAsync(report, geo->d_scalars, sizeof(double) * n_norms, cudaMemcpyDeviceToHost, st));
+        TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return timer.finish();
+}
+
+tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *f, const tnlm_params *p, void *stream)
+{
+    TNLM_TRY(check_params(p, false));
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, p->d, p->M, p->h, p->mu));
+    if (!g || !f) return arg_error("g and f must not be NULL");
+    if (g == f) return arg_error("g and f must not alias");
+    cudaStream_t st = as_stream(stream);
+    const size_t n = (size_t)np * nx * ny * nz;
+    if (p->n_outer == 0) {
+        TNLM_TRY_CUDA(cudaMemcpyAsync(f, g, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        return TNLM_OK;
+    }
+    float *tmp = nullptr;
+    if (p->n_outer > 1) {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(float) * n, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMallocAsync of the ping-pong buffer (%zu bytes) failed", sizeof(float) * n);
+            return TNLM_ERR_OOM;
+        }
+    }
+    // f^(0) = g; sweep s writes f when (n_outer - 1 - s) is even, so the last sweep lands in f
+    const float *src = g;
+    tnlm_status s = TNLM_OK;
+    for (int k = 0; k < p->n_outer && s == TNLM_OK; ++k) {
+        float *dst = ((p->n_outer - 1 - k) % 2 == 0) ? f : tmp;
+        s = launch_sweep(nx, ny, nz, np, src, src, g, dst, p->d, p->M, p->h, p->mu, p->clip_nonneg, st);
+        src = dst;
+    }
+    if (tmp) cudaFreeAsync(tmp, st);
+    return s;
+}
+
+tnlm_status tnlm_operator_norm(tnlm_geometry *geo, float *x, int n_iter, double *L_out, void *stream)
+{
+    if (!geo || !x || !L_out) return arg_error("geometry, x and L_out must not be NULL");
+    if (n_iter < 1) return arg_error("n_iter must be >= 1");
+    TNLM_TRY(ensure_workspace(geo, false, 2));
+    const KGeom &kg = geo->kg;
+    cudaStream_t st = as_stream(stream);
+    const long long nv = (long long)kg.np * kg.nvox;
+    const long long npr = (long long)geo->n_views_total * kg.npix;
+    for (int it = 0; it < n_iter; ++it) {
+        TNLM_TRY(launch_sumsq(x, nv, geo->d_part, (int)geo->part_len, geo->d_scalars, st));
+        TNLM_TRY(launch_normalize(x, nv, geo->d_scalars, st));
+        TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, x, nullptr, geo->d_r, nullptr, 0, st));
+        TNLM_TRY(launch_sumsq(geo->d_r, npr, geo->d_part, (int)geo->part_len, geo->d_scalars + 1, st));
+        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, x, x, 1.0f, 0.0f, false, st));
+    }
+    TNLM_TRY_CUDA(cudaMemcpyAsync(L_out, geo->d_scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_set_stage_timing(tnlm_geometry *g, int enable)
+{
+    if (!g) return arg_error("geometry must not be NULL");
+    g->timing = enable ? 1 : 0;
+    for (int s = 0; s < 3; ++s) {
+        g->stage_ms[s] = 0.0;
+        g->stage_launches[s] = 0;
+    }
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_get_stage_timing(const tnlm_geometry *g, double ms[3], long long launches[3])
+{
+    if (!g || !ms || !launches) return arg_error("geometry, ms and launches must not be NULL");
+    for (int s = 0; s < 3; ++s) {
+        ms[s] = g->stage_ms[s];
+        launches[s] = g->stage_launches[s];
+    }
+    return TNLM_OK;
+}
+
+}  // extern "C"

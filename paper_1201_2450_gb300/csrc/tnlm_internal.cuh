@@ -1,0 +1,107 @@
+// Internal declarations shared by the translation units of libtnlm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "tnlm.h"
+
+namespace tnlm {
+
+// Kernel-side scan geometry, passed by value (all lengths in mm).
+struct KGeom {
+    int nx, ny, nz, np;
+    float dx, dy, dz;
+    float inv_dx, inv_dy, inv_dz;
+    float hx, hy, hz;        // half voxel sizes
+    float b0x, b0y, b0z;     // volume corner (lower faces of voxel 0)
+    int nu, nv;
+    float du, dv, inv_du, inv_dv;
+    float u_off, v_off;
+    float uc, vc;            // (nu-1)/2, (nv-1)/2
+    float sad, sdd, inv_sdd;
+    float alpha0;            // sad / sdd: ray parameter of the isocentre plane
+    long long nvox;          // nx*ny*nz
+    long long npix;          // nu*nv
+};
+
+// One projection view: rotation and owning phase.
+struct ViewGeom {
+    float c, s;   // cos, sin of the view angle
+    int phase;
+    int pad;
+};
+
+void set_error(const char *fmt, ...);
+
+#define TNLM_TRY_CUDA(call)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            ::tnlm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return TNLM_ERR_CUDA;                                                                 \
+        }                                                                                         \
+    } while (0)
+
+#define TNLM_TRY(call)                       \
+    do {                                     \
+        tnlm_status s_ = (call);             \
+        if (s_ != TNLM_OK) return s_;        \
+    } while (0)
+
+// Kernel launchers (host side).
+// mode 0: out = P vol.  mode 1: out = (P vol - y) * |ray| with FP64 per-block
+// partial sums of (P vol - y)^2 in partials[forward_blocks(g)].
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
+                           const float *y, float *out, double *partials, int mode, cudaStream_t st);
+long long forward_blocks(const KGeom &kg, int n_views_total);
+
+// vout = beta * vin + alpha * P^T proj.  scaled: proj already multiplied by
+// the ray length |source -> pixel| (the residual form written by mode 1).
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const float *vin, float *vout, float alpha, float beta, bool scaled,
+                               cudaStream_t st);
+
+tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
+                         float *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
+tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,
+                           cudaStream_t st);
+
+// FP64 reductions: *result = sum(partials[0..n)); sum of squares of x.
+tnlm_status launch_sum_partials(const double *partials, long long n, double *result, cudaStream_t st);
+tnlm_status launch_sumsq(const float *x, long long n, double *scratch, int scratch_len, double *result,
+                         cudaStream_t st);
+// x *= 1 / sqrt(*nrm2) (device scalar)
+tnlm_status launch_normalize(float *x, long long n, const double *nrm2, cudaStream_t st);
+
+int sumsq_scratch_len();
+
+tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float h, float mu);
+
+}  // namespace tnlm
+
+// The opaque handle.
+struct tnlm_geometry {
+    tnlm::KGeom kg;
+    int device;
+    int n_views_total;
+    std::vector<int> n_views;
+    std::vector<int> view_off;        // [np+1]
+    std::vector<double> angles;
+    tnlm::ViewGeom *d_views = nullptr;
+    int *d_view_off = nullptr;
+    // workspace (allocated on first use)
+    float *d_r = nullptr;             // sum(n_views) * npix
+    float *d_g = nullptr;             // np * nvox
+    float *d_tmp = nullptr;           // np * nvox (gj_start = 1 only)
+    double *d_part = nullptr;         // forward-projector partial sums
+    long long part_len = 0;
+    double *d_scalars = nullptr;      // reduction results
+    long long scalars_len = 0;
+    // instrumentation
+    int timing = 0;
+    double stage_ms[3] = {0, 0, 0};
+    long long stage_launches[3] = {0, 0, 0};
+};

@@ -1,0 +1,340 @@
+"""GPU parity: every C-ABI call against the FP64 oracle on seeded inputs.
+
+Tolerance: relative L2 error <= 1e-5 for the FP32 paths (elementwise
+comparison over the whole output), as the method's FP32 target states.
+Sizes span several CUDA tiles with ragged tails (projector tiles 32 x 4
+pixels, transpose tiles 32 x 4 columns x 8 slices, sweep tiles 8 x 8 x 4).
+At the full benchmark size (10 x 256^2 x 64, 36 views x 512 x 384) outputs
+are checked on sampled rays / voxels the oracle computes one by one and via
+the adjoint identity, which holds at any size."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1201_2450_gb300 as tnlm
+from paper_1201_2450_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    tnlm.build()
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+GEOMS = {
+    "ragged_uneven": synth.make_geometry(nx=37, ny=29, nz=11, dx=1.0, dy=1.1, dz=0.9, cx=0.7, cy=-1.3, cz=0.4,
+                                         nu=70, nv=13, du=1.3, dv=1.7, u_off=0.9, v_off=-0.6, sad=300.0,
+                                         sdd=450.0, n_phases=3, views_per_phase=[4, 5, 3], angle_offset=0.03),
+    "c1": synth.C1.geometry(),
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_project_matches_oracle(ora, name):
+    geom = GEOMS[name]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    x = synth.uniform(G.vol_shape, 101)
+    p = tnlm.tnlm_project(G, cuda(x)).cpu().numpy()
+    p_ref = ora.project(OG, x)
+    assert rel_l2(p, p_ref) <= RTOL
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_backproject_matches_oracle(ora, name):
+    geom = GEOMS[name]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    y = synth.uniform(G.proj_shape, 102)
+    v0 = synth.uniform(G.vol_shape, 103)
+    out = tnlm.tnlm_backproject(G, cuda(y), cuda(v0), alpha=2.0, beta=0.5).cpu().numpy()
+    ref = 0.5 * v0.astype(np.float64) + 2.0 * ora.backproject(OG, y)
+    assert rel_l2(out, ref) <= RTOL
+    bt = tnlm.tnlm_backproject(G, cuda(y)).cpu().numpy()
+    assert rel_l2(bt, ora.backproject(OG, y)) <= RTOL
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_adjoint_identity_gpu_pair(name):
+    G = tnlm.Geometry(GEOMS[name])
+    x = cuda(synth.uniform(G.vol_shape, 104))
+    y = cuda(synth.uniform(G.proj_shape, 105))
+    px = tnlm.tnlm_project(G, x)
+    bty = tnlm.tnlm_backproject(G, y)
+    lhs = float((px.double() * y.double()).sum())
+    rhs = float((x.double() * bty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * float(px.double().norm() * y.double().norm())
+
+
+def test_project_odd_detector_face_rays(ora):
+    """Odd nu, nv put pixel rays exactly in voxel face planes at multiples of
+    90 degrees; away from such exact ties the pair still matches."""
+    geom = synth.make_geometry(nx=16, ny=16, nz=8, dx=1.0, nu=33, nv=17, du=1.0, sad=200, sdd=300, n_phases=2,
+                               views_per_phase=3, angle_offset=0.01)
+    G = tnlm.Geometry(geom)
+    x = synth.uniform(G.vol_shape, 106)
+    assert rel_l2(tnlm.tnlm_project(G, cuda(x)).cpu().numpy(), ora.project(ora.Geometry(geom), x)) <= RTOL
+
+
+WEIGHT_CASES = [((3, 7, 10, 12), 1, 2, 0.5), ((2, 5, 6, 9), 2, 1, 0.8), ((4, 4, 4, 4), 0, 2, 0.3),
+                ((2, 6, 5, 7), 1, 3, 0.5)]
+
+
+@pytest.mark.parametrize("shape,d,M,h", WEIGHT_CASES)
+def test_weights_match_oracle(ora, shape, d, M, h):
+    a = synth.uniform(shape, 107)
+    w = tnlm.tnlm_weights(cuda(a), d, M, h).cpu().numpy()
+    ref = ora.weights(a, d, M, h)
+    assert rel_l2(w, ref) <= RTOL
+    np.testing.assert_allclose(w.sum(-1), 1.0, rtol=1e-5)
+
+
+def test_weights_hand_fixture():
+    """The 2-phase 4^3 fixture of tests/golden (hand-derived closed forms)."""
+    a = np.zeros((2, 4, 4, 4), np.float32)
+    a[0, 1, 1, 1] = 1.0
+    a[1, 1, 1, 2] = 1.0
+    w = tnlm.tnlm_weights(cuda(a), 1, 1, 1.0).cpu().numpy()
+    assert w[0, 0, 1, 1, 1][14] == pytest.approx(1.0 / (1 + 9 * math.exp(-0.5) + 17 * math.exp(-1)), rel=1e-6)
+    assert w[0, 0, 0, 0, 0][14] == pytest.approx(1.0 / (1 + 4 * math.exp(-0.5) + 3 * math.exp(-1)), rel=1e-6)
+
+
+def _sweep_inputs(shape, seed, kind):
+    if kind == "smooth":
+        a = synth.smooth_volume(shape, seed) + synth.normal(shape, seed + 1, 0.002)
+        v = a + synth.normal(shape, seed + 2, 0.001)
+        g = a + synth.normal(shape, seed + 3, 0.003)
+        return a, v, g, 0.02
+    a = synth.uniform(shape, seed)
+    return a, synth.uniform(shape, seed + 1), synth.uniform(shape, seed + 2) - 0.3, 0.6
+
+
+SWEEP_CASES = [
+    ((3, 9, 13, 19), 1, 1, "smooth", 0), ((2, 9, 13, 19), 1, 2, "uniform", 1), ((4, 9, 13, 19), 1, 3, "smooth", 1),
+    ((3, 7, 10, 11), 2, 3, "smooth", 0), ((3, 7, 10, 11), 2, 2, "uniform", 0), ((2, 5, 9, 8), 0, 2, "uniform", 0),
+    ((3, 6, 9, 10), 3, 1, "smooth", 1), ((5, 4, 8, 8), 1, 0, "uniform", 0), ((3, 9, 17, 33), 2, 1, "smooth", 1),
+]
+
+
+@pytest.mark.parametrize("shape,d,M,kind,clip", SWEEP_CASES)
+def test_gauss_jacobi_matches_oracle(ora, shape, d, M, kind, clip):
+    a, v, g, h = _sweep_inputs(shape, 110, kind)
+    mu = 0.8
+    out = tnlm.tnlm_gauss_jacobi(cuda(a), cuda(v), cuda(g), d, M, h, mu, clip).cpu().numpy()
+    ref = ora.gj_sweep(a, v, g, d, M, h, mu, clip)
+    assert rel_l2(out, ref) <= RTOL
+
+
+def test_gauss_jacobi_window_zero_closed_form():
+    """M = 0: the window is the voxel itself, so Eq. 8 reduces to
+    (mu g_i + v_{i+1} + v_{i-1}) / (2 + mu) whatever the weights."""
+    shape = (3, 5, 6, 7)
+    a, v, g = (synth.uniform(shape, s) for s in (120, 121, 122))
+    out = tnlm.tnlm_gauss_jacobi(cuda(a), cuda(v), cuda(g), 1, 0, 0.1, 0.5).cpu().numpy()
+    ref = (0.5 * g + np.roll(v, -1, 0) + np.roll(v, 1, 0)) / 2.5
+    np.testing.assert_allclose(out, ref, rtol=2e-6, atol=1e-7)
+
+
+def test_gauss_jacobi_single_voxel_volume():
+    shape = (2, 1, 1, 1)
+    a, v, g = (synth.uniform(shape, s) for s in (123, 124, 125))
+    out = tnlm.tnlm_gauss_jacobi(cuda(a), cuda(v), cuda(g), 2, 3, 0.1, 1.0).cpu().numpy()
+    ref = (g + 2 * v[::-1]) / 3.0
+    np.testing.assert_allclose(out, ref, rtol=2e-6)
+
+
+def test_enhance_matches_oracle(ora):
+    shape = (4, 12, 20, 24)
+    cfg = synth.EnhanceConfig("t", 4, (24, 20, 12), 1.0, 0.002, 0.003, 36, 2, 3, 0.04, 1.0, 3, 130)
+    g, _ = synth.enhance_input(cfg)
+    g = g.numpy()
+    p = tnlm.Params(d=2, M=3, h=0.04, mu=1.0, n_outer=3, clip_nonneg=0)
+    f = tnlm.tnlm_enhance(cuda(g), p).cpu().numpy()
+    ref = ora.enhance(g, 2, 3, 0.04, 1.0, 3)
+    assert rel_l2(f, ref) <= RTOL
+    # zero sweeps copy g; two sweeps end in the output buffer too
+    p0 = tnlm.Params(d=2, M=3, h=0.04, mu=1.0, n_outer=0, clip_nonneg=0)
+    np.testing.assert_array_equal(tnlm.tnlm_enhance(cuda(g), p0).cpu().numpy(), g)
+    p2 = tnlm.Params(d=1, M=2, h=0.04, mu=1.0, n_outer=2, clip_nonneg=0)
+    assert rel_l2(tnlm.tnlm_enhance(cuda(g), p2).cpu().numpy(), ora.enhance(g, 1, 2, 0.04, 1.0, 2)) <= RTOL
+
+
+def _recon_case(ora, cfg, n_outer, seed=7):
+    pb = synth.recon_problem(cfg)
+    OG = ora.Geometry(pb.geom)
+    L = ora.power_norm(OG, synth.uniform(OG.vol_shape, seed), 30)
+    tau = float(np.float32(1.0 / L))
+    y = pb.y.numpy()
+    f_ref, rep_ref = ora.reconstruct(OG, y, np.zeros(OG.vol_shape), tau, cfg.d, cfg.M, cfg.h, cfg.mu, n_outer,
+                                     with_report=True)
+    G = tnlm.Geometry(pb.geom)
+    f = torch.zeros(G.vol_shape, device="cuda")
+    p = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=n_outer)
+    _, rep = tnlm.tnlm_reconstruct(G, cuda(y), f, p, report=True)
+    return f.cpu().numpy(), f_ref, rep, rep_ref
+
+
+def test_reconstruct_c1_full(ora):
+    """Config C1 in full: 4 x 32^3, 20 views x 64 x 48, d=1, M=2, 5 iterations."""
+    f, f_ref, rep, rep_ref = _recon_case(ora, synth.C1, synth.C1.n_outer)
+    assert rel_l2(f, f_ref) <= RTOL
+    np.testing.assert_allclose(rep, rep_ref, rtol=RTOL)
+    assert np.all(f >= 0)
+
+
+C2_TINY = synth.ReconConfig("NCAT-shaped reduced 10x32x32x8, 9 views x 64x48", 10, (32, 32, 8), 16.0, 9, (64, 48),
+                            6.24, 5e4, 1, 3, 0.02, 1.0, 50, "thorax", 1002)
+
+
+def test_reconstruct_c2_structure_full_length(ora):
+    """C2's structure (10 phases, d=1, M=3, 50 FBS iterations) at a reduced grid."""
+    f, f_ref, rep, rep_ref = _recon_case(ora, C2_TINY, C2_TINY.n_outer)
+    err = rel_l2(f, f_ref)
+    assert err <= RTOL, err
+    np.testing.assert_allclose(rep, rep_ref, rtol=RTOL)
+
+
+def test_reconstruct_gj_start_and_inner_steps(ora):
+    geom = GEOMS["ragged_uneven"]
+    OG = ora.Geometry(geom)
+    G = tnlm.Geometry(geom)
+    y = synth.uniform(G.proj_shape, 140) * 0.5
+    f0 = synth.smooth_volume(G.vol_shape, 141)
+    tau = 1e-4
+    ref = ora.reconstruct(OG, y, f0, tau, 1, 2, 0.02, 0.7, 2, n_inner=3, clip=0, gj_start=1)
+    f = cuda(f0)
+    tnlm.tnlm_reconstruct(G, cuda(y), f, tnlm.Params(d=1, M=2, h=0.02, mu=0.7, tau=tau, n_outer=2, n_inner=3,
+                                                     clip_nonneg=0, gj_start=1))
+    assert rel_l2(f.cpu().numpy(), ref) <= RTOL
+    # n_outer = 0 leaves f untouched
+    f = cuda(f0)
+    tnlm.tnlm_reconstruct(G, cuda(y), f, tnlm.Params(tau=tau, n_outer=0))
+    np.testing.assert_array_equal(f.cpu().numpy(), f0)
+
+
+def test_operator_norm_matches_oracle(ora):
+    geom = GEOMS["ragged_uneven"]
+    x0 = synth.uniform((3, 11, 29, 37), 150)
+    L_ref = ora.power_norm(ora.Geometry(geom), x0, 40)
+    G = tnlm.Geometry(geom)
+    L = tnlm.tnlm_operator_norm(G, cuda(x0), 40)
+    assert L == pytest.approx(L_ref, rel=1e-4)
+
+
+def test_stage_timing_counts_launches():
+    geom = GEOMS["c1"]
+    G = tnlm.Geometry(geom)
+    G.set_stage_timing(True)
+    y = cuda(synth.uniform(G.proj_shape, 160))
+    f = torch.zeros(G.vol_shape, device="cuda")
+    tnlm.tnlm_reconstruct(G, y, f, tnlm.Params(tau=1e-3, n_outer=3, n_inner=2))
+    ms, n = G.stage_timing()
+    assert n == [6, 6, 3] and all(m > 0 for m in ms)
+
+
+def test_invalid_arguments_raise():
+    G = tnlm.Geometry(GEOMS["c1"])
+    f = torch.zeros(G.vol_shape, device="cuda")
+    y = torch.zeros(G.proj_shape, device="cuda")
+    with pytest.raises(tnlm.TnlmError):
+        tnlm.tnlm_reconstruct(G, y, f, tnlm.Params(tau=1e-3, M=7))
+    with pytest.raises(tnlm.TnlmError):
+        tnlm.tnlm_reconstruct(G, y, f, tnlm.Params(tau=1e-3, n_inner=0))
+    with pytest.raises(ValueError):
+        tnlm.tnlm_project(G, f.double())
+
+
+# ---------------------------------------------------------------------------
+# full benchmark size (C2: 10 x 256^2 x 64, 36 views x 512 x 384)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c2_full():
+    pb = synth.recon_problem(synth.C2, device="cuda")
+    return pb
+
+
+def test_full_size_projector_sampled_rays(ora, c2_full):
+    pb = c2_full
+    G = tnlm.Geometry(pb.geom)
+    vol = (pb.truth + torch.from_numpy(synth.normal(G.vol_shape, 170, 0.002)).cuda()).contiguous()
+    p = tnlm.tnlm_project(G, vol).cpu().numpy()
+    OG = ora.Geometry(pb.geom)
+    vh = vol.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(171)
+    idx = [(int(rng.integers(G.proj_shape[0])), int(rng.integers(G.proj_shape[2])),
+            int(rng.integers(G.proj_shape[1]))) for _ in range(256)]
+    got = np.array([p[v, iv, iu] for v, iu, iv in idx])
+    ref = np.array([ora.project_ray(OG, vh, v, iu, iv) for v, iu, iv in idx])
+    assert rel_l2(got, ref) <= RTOL
+
+
+def test_full_size_backprojector_adjoint_and_sampled_voxels(ora, c2_full):
+    pb = c2_full
+    G = tnlm.Geometry(pb.geom)
+    y = pb.y
+    bt = tnlm.tnlm_backproject(G, y)
+    x = (pb.truth + 0.01).contiguous()
+    px = tnlm.tnlm_project(G, x)
+    lhs = float((px.double() * y.double()).sum())
+    rhs = float((x.double() * bt.double()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * float(px.double().norm() * y.double().norm())
+    OG = ora.Geometry(pb.geom)
+    yh = y.cpu().numpy().astype(np.float64)
+    bth = bt.cpu().numpy()
+    rng = np.random.default_rng(172)
+    pts = [(int(rng.integers(10)), int(rng.integers(64)), int(rng.integers(64, 192)), int(rng.integers(64, 192)))
+           for _ in range(12)]
+    got = np.array([bth[ph, z, yy, xx] for ph, z, yy, xx in pts])
+    ref = np.array([ora.backproject_voxel(OG, yh, ph, xx, yy, z) for ph, z, yy, xx in pts])
+    assert rel_l2(got, ref) <= RTOL
+
+
+def test_full_size_sweep_sampled_voxels(ora, c2_full):
+    pb = c2_full
+    a = (pb.truth + torch.from_numpy(synth.normal(pb.truth.shape, 173, 0.002)).cuda()).contiguous()
+    cfg = synth.C2
+    out = tnlm.tnlm_gauss_jacobi(a, a, a, cfg.d, cfg.M, cfg.h, cfg.mu, 1).cpu().numpy()
+    ah = a.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(174)
+    pts = [(int(rng.integers(10)), int(rng.integers(64)), int(rng.integers(256)), int(rng.integers(256)))
+           for _ in range(300)]
+    got = np.array([out[ph, z, yy, xx] for ph, z, yy, xx in pts])
+    ref = np.array([ora.gj_voxel(ah, ah, ah, ph, xx, yy, z, cfg.d, cfg.M, cfg.h, cfg.mu, 1) for ph, z, yy, xx in pts])
+    assert rel_l2(got, ref) <= RTOL
+
+
+def test_full_size_fused_iteration_equals_composed_calls(c2_full):
+    """One tnlm_reconstruct iteration in the benchmark's launch configuration
+    (fused residual, scaled transpose, sweep with positivity) equals the same
+    iteration composed from tnlm_project / tnlm_backproject /
+    tnlm_gauss_jacobi."""
+    pb = c2_full
+    G = tnlm.Geometry(pb.geom)
+    cfg = synth.C2
+    f0 = (pb.truth * 0.9).contiguous()
+    tau = 2e-6
+    f = f0.clone()
+    tnlm.tnlm_reconstruct(G, pb.y, f, tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=1))
+    r = tnlm.tnlm_project(G, f0) - pb.y
+    g = tnlm.tnlm_backproject(G, r.contiguous(), f0.clone(), alpha=-tau, beta=1.0)
+    f2 = tnlm.tnlm_gauss_jacobi(g, g, g, cfg.d, cfg.M, cfg.h, cfg.mu, 1)
+    assert rel_l2(f.cpu().numpy(), f2.cpu().numpy()) <= RTOL
