@@ -145,6 +145,28 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, cons
 tnlm_status tnlm_enhance(int nx, int ny, int nz, int n_phases, const float *g, float *f, const tnlm_params *params,
                          void *stream);
 
+/* TNLM-E without any device allocation, for callers that cannot allocate
+ * device memory (e.g. an application whose memory pool owns the GPU's
+ * memory budget from start-up, so an allocation by the library would fail
+ * or break that budget).  The paper has no counterpart: this is the same
+ * computation as tnlm_enhance, but its ping-pong image lives in a fixed
+ * file-scope device array of 4 Mi floats (16 MiB) instead of a
+ * cudaMallocAsync buffer.  Limits and behaviour:
+ *  - n_phases * nx * ny * nz must not exceed 4194304 (TNLM_ERR_ARG with a
+ *    message otherwise; use tnlm_enhance for larger problems);
+ *  - the array exists on every GPU that loads the library until the process
+ *    exits;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call on a device shares the one array, so calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race and give
+ *    wrong results: serialise them.  Each sweep overwrites the whole array
+ *    before reading it, so nothing left by an earlier call needs clearing.
+ * Arguments are those of tnlm_enhance. */
+tnlm_status tnlm_enhance_noalloc(int nx, int ny, int nz, int n_phases, const float *g, float *f,
+                                 const tnlm_params *params, void *stream);
+
 /* Estimate L = ||P||_2^2 (so tau = 1/L for the (P1) step) by n_iter power
  * iterations on P^T P from the start image x ([N_p][nz][ny][nx], device,
  * overwritten).  *L_out (host) receives the Rayleigh quotient ||P x||^2 of

@@ -26,7 +26,8 @@ from ._build import build
 
 __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
-    "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_operator_norm",
+    "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
+    "tnlm_operator_norm",
     "reconstruct_host", "library_path",
 ]
 
@@ -105,6 +106,7 @@ def _load():
             "tnlm_gauss_jacobi": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
+            "tnlm_enhance_noalloc": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -269,6 +271,17 @@ def tnlm_enhance(g: torch.Tensor, params: Params, out: torch.Tensor | None = Non
     p = params._c()
     _check(_load().tnlm_enhance(nx, ny, nz, np_, _dev(g, "g"), _dev(out, "f", g.device, g.shape), C.byref(p),
                                 _stream(stream)), "tnlm_enhance")
+    return out
+
+
+def tnlm_enhance_noalloc(g: torch.Tensor, params: Params, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """TNLM-E that allocates nothing on the device: the caller provides the
+    output and the library's fixed 16 MiB scratch array holds the ping-pong
+    image (at most 4 Mi voxels over all phases)."""
+    np_, nz, ny, nx = g.shape
+    p = params._c()
+    _check(_load().tnlm_enhance_noalloc(nx, ny, nz, np_, _dev(g, "g"), _dev(out, "f", g.device, g.shape),
+                                        C.byref(p), _stream(stream)), "tnlm_enhance_noalloc")
     return out
 
 
