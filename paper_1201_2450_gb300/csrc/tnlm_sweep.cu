@@ -115,6 +115,236 @@ __global__ void __launch_bounds__(kTX *kTY *kTZ)
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_sweep_box: the same sweep with the patch distance evaluated as a
+// separable box sum.  For a fixed window offset delta,
+//   D_delta(x) = sum_{o in [-d,d]^3} s_delta(x + o),
+//   s_delta(z) = (a_i(clamp z) - a_j(clamp(z + delta)))^2,
+// which is the definition of Eq. 3 / Eq. 9 regrouped (clamping depends on z
+// only).  A warp's 32 lanes span x (lanes d .. 31-d are outputs, the others
+// supply the x halo) and sum along x with shuffles; each thread holds a
+// BY x BZ block of outputs in (y, z) and sums along z and y in registers.
+// The images of the neighbour phase are staged in shared memory per
+// direction; the thread's own patch block of phase i stays in registers for
+// all offsets.
+// ---------------------------------------------------------------------------
+template <int D_, int M_, int BY, int BZ>
+struct BoxCfg {
+    static constexpr int WY = 4, WZ = 2;           // warps per CTA along y and z
+    static constexpr int NT = 32 * WY * WZ;
+    static constexpr int TXO = 32 - 2 * D_;         // outputs per warp row
+    static constexpr int TY = WY * BY, TZ = WZ * BZ;
+    static constexpr int SY = BY + 2 * D_, SZ = BZ + 2 * D_;
+    static constexpr int AJX = 32 + 2 * M_, AJY = TY + 2 * (M_ + D_), AJZ = TZ + 2 * (M_ + D_);
+    static constexpr int VJX = 32 + 2 * M_, VJY = TY + 2 * M_, VJZ = TZ + 2 * M_;
+    static constexpr size_t SMEM = sizeof(float) * ((size_t)AJX * AJY * AJZ + (size_t)VJX * VJY * VJZ);
+};
+
+template <int D_>
+__device__ __forceinline__ float xbox(float b)
+{
+    const unsigned F = 0xffffffffu;
+    if constexpr (D_ == 0) {
+        return b;
+    } else if constexpr (D_ == 1) {
+        return __shfl_up_sync(F, b, 1) + b + __shfl_down_sync(F, b, 1);
+    } else if constexpr (D_ == 2) {
+        const float p = b + __shfl_down_sync(F, b, 1);  // b(x) + b(x+1)
+        return __shfl_up_sync(F, p, 2) + p + __shfl_down_sync(F, b, 2);
+    } else {
+        float acc = b;
+#pragma unroll
+        for (int t = 1; t <= D_; ++t) acc += __shfl_up_sync(F, b, t) + __shfl_down_sync(F, b, t);
+        return acc;
+    }
+}
+
+template <int D_, int M_, int BY, int BZ, bool INTERIOR>
+__device__ __forceinline__ void box_direction(const float (&ai)[BY + 2 * D_][BZ + 2 * D_], const float *s_aj,
+                                              const float *s_vj, int lane, int wy, int wz, int x, int yb, int zb,
+                                              int nx, int ny, int nz, float c2, float (&res)[BY][BZ])
+{
+    using C = BoxCfg<D_, M_, BY, BZ>;
+    float mref[BY][BZ], N[BY][BZ], Z[BY][BZ];
+#pragma unroll
+    for (int j = 0; j < BY; ++j)
+#pragma unroll
+        for (int k = 0; k < BZ; ++k) {
+            mref[j][k] = FLT_MAX;
+            N[j][k] = 0.f;
+            Z[j][k] = 0.f;
+        }
+    for (int dy = -M_; dy <= M_; ++dy) {
+        bool vy[BY];
+#pragma unroll
+        for (int j = 0; j < BY; ++j) vy[j] = INTERIOR || (unsigned)(yb + j + dy) < (unsigned)ny;
+        for (int dx = -M_; dx <= M_; ++dx) {
+            const bool vx = INTERIOR || (unsigned)(x + dx) < (unsigned)nx;
+            // neighbour-phase values along z for this (dy, dx): a sliding window of SZ rows
+            const float *paj = s_aj + (wy * BY + dy + M_) * C::AJX + lane + dx + M_;
+            const float *pvj = s_vj + (wy * BY + dy + M_) * C::VJX + lane + dx + M_;
+            float aw[2 * M_ + C::SZ][C::SY];
+            float vw[2 * M_ + BZ][BY];
+#pragma unroll
+            for (int r = 0; r < C::SZ - 1; ++r)
+#pragma unroll
+                for (int yy = 0; yy < C::SY; ++yy) aw[r][yy] = paj[((wz * BZ + r) * C::AJY + yy) * C::AJX];
+#pragma unroll
+            for (int r = 0; r < BZ - 1; ++r)
+#pragma unroll
+                for (int j = 0; j < BY; ++j) vw[r][j] = pvj[((wz * BZ + r) * C::VJY + j) * C::VJX];
+#pragma unroll
+            for (int q = 0; q <= 2 * M_; ++q) {  // q = dz + M
+                {
+                    const int r = q + C::SZ - 1;
+#pragma unroll
+                    for (int yy = 0; yy < C::SY; ++yy) aw[r][yy] = paj[((wz * BZ + r) * C::AJY + yy) * C::AJX];
+                    const int rv = q + BZ - 1;
+#pragma unroll
+                    for (int j = 0; j < BY; ++j) vw[rv][j] = pvj[((wz * BZ + rv) * C::VJY + j) * C::VJX];
+                }
+                // z box sums of the squared differences, row by row
+                float bz[C::SY][BZ];
+#pragma unroll
+                for (int yy = 0; yy < C::SY; ++yy) {
+                    float srow[C::SZ];
+#pragma unroll
+                    for (int zz = 0; zz < C::SZ; ++zz) {
+                        const float t = ai[yy][zz] - aw[q + zz][yy];
+                        srow[zz] = t * t;
+                    }
+#pragma unroll
+                    for (int k = 0; k < BZ; ++k) {
+                        float acc = srow[k];
+#pragma unroll
+                        for (int t = 1; t <= 2 * D_; ++t) acc += srow[k + t];
+                        bz[yy][k] = acc;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < BY; ++j)
+#pragma unroll
+                    for (int k = 0; k < BZ; ++k) {
+                        float acc = bz[j][k];
+#pragma unroll
+                        for (int t = 1; t <= 2 * D_; ++t) acc += bz[j + t][k];
+                        const float Dv = xbox<D_>(acc);  // patch distance of output (j, k) at this offset
+                        const bool valid = INTERIOR || (vx && vy[j] && (unsigned)(zb + k + q - M_) < (unsigned)nz);
+                        if (valid) {
+                            const float a = fmaf(-Dv, c2, mref[j][k]);  // log2 weight vs the reference
+                            float e;
+                            if (a > kRescale) {  // candidate beats the reference by 2^kRescale: move it
+                                const float sc = ex2(-a);
+                                N[j][k] *= sc;
+                                Z[j][k] *= sc;
+                                mref[j][k] = Dv * c2;
+                                e = 1.f;
+                            } else {
+                                e = ex2(a);
+                            }
+                            N[j][k] = fmaf(e, vw[q + k][j], N[j][k]);
+                            Z[j][k] += e;
+                        }
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < BY; ++j)
+#pragma unroll
+        for (int k = 0; k < BZ; ++k) res[j][k] += N[j][k] / Z[j][k];
+}
+
+template <int D_, int M_, int BY, int BZ>
+__global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
+    k_sweep_box(int nx, int ny, int nz, int np, int ntx, int nty, int ntz, const float *__restrict__ wsrc,
+                const float *__restrict__ vals, const float *__restrict__ g, float *__restrict__ out, float c2,
+                float mu, int clip)
+{
+    using C = BoxCfg<D_, M_, BY, BZ>;
+    extern __shared__ float sm[];
+    float *s_aj = sm;
+    float *s_vj = sm + C::AJX * C::AJY * C::AJZ;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wy = warp % C::WY, wz = warp / C::WY;
+    int b = blockIdx.x;
+    const int tx_i = b % ntx;
+    b /= ntx;
+    const int ty_i = b % nty;
+    b /= nty;
+    const int tz_i = b % ntz;
+    const int i = b / ntz;
+    const int X0 = tx_i * C::TXO, Y0 = ty_i * C::TY, Z0 = tz_i * C::TZ;
+    const int x = X0 - D_ + lane;
+    const int yb = Y0 + wy * BY, zb = Z0 + wz * BZ;
+    const long long nvox = (long long)nx * ny * nz;
+    const bool interior = X0 - M_ >= 0 && X0 + C::TXO - 1 + M_ < nx && Y0 - M_ >= 0 && Y0 + C::TY - 1 + M_ < ny &&
+                          Z0 - M_ >= 0 && Z0 + C::TZ - 1 + M_ < nz;
+
+    // this thread's patch block of phase i (clamped reads), kept for all offsets
+    float ai[C::SY][C::SZ];
+    {
+        const float *src = wsrc + i * nvox;
+        const int cx = clampi(x, nx);
+#pragma unroll
+        for (int yy = 0; yy < C::SY; ++yy)
+#pragma unroll
+            for (int zz = 0; zz < C::SZ; ++zz)
+                ai[yy][zz] = __ldg(src + ((long long)clampi(zb - D_ + zz, nz) * ny + clampi(yb - D_ + yy, ny)) * nx + cx);
+    }
+    float res[BY][BZ];
+#pragma unroll
+    for (int j = 0; j < BY; ++j)
+#pragma unroll
+        for (int k = 0; k < BZ; ++k) res[j][k] = 0.f;
+
+    for (int dir = 0; dir < 2; ++dir) {
+        const int jp = dir == 0 ? (i + 1) % np : (i - 1 + np) % np;
+        __syncthreads();
+        stage_clamped(s_aj, wsrc + jp * nvox, X0 - D_ - M_, Y0 - D_ - M_, Z0 - D_ - M_, C::AJX, C::AJY, C::AJZ, nx, ny,
+                      nz, tid, C::NT);
+        stage_clamped(s_vj, vals + jp * nvox, X0 - D_ - M_, Y0 - M_, Z0 - M_, C::VJX, C::VJY, C::VJZ, nx, ny, nz, tid,
+                      C::NT);
+        __syncthreads();
+        if (interior)
+            box_direction<D_, M_, BY, BZ, true>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
+        else
+            box_direction<D_, M_, BY, BZ, false>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
+    }
+    if (lane >= D_ && lane < 32 - D_ && x < nx) {
+        const float inv = 1.f / (2.f + mu);
+#pragma unroll
+        for (int j = 0; j < BY; ++j)
+#pragma unroll
+            for (int k = 0; k < BZ; ++k) {
+                const int y = yb + j, z = zb + k;
+                if (y < ny && z < nz) {
+                    const long long o = i * nvox + ((long long)z * ny + y) * nx + x;
+                    float f = (mu * __ldg(g + o) + res[j][k]) * inv;  // Eq. 8
+                    if (clip) f = fmaxf(f, 0.f);                     // positivity (TNLM-R step 4)
+                    out[o] = f;
+                }
+            }
+    }
+}
+
+template <int D_, int M_>
+bool launch_box(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g, float *out,
+                float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
+{
+    constexpr int BY = 2, BZ = 4;
+    using C = BoxCfg<D_, M_, BY, BZ>;
+    const int ntx = (nx + C::TXO - 1) / C::TXO, nty = (ny + C::TY - 1) / C::TY, ntz = (nz + C::TZ - 1) / C::TZ;
+    const long long blocks = (long long)ntx * nty * ntz * np;
+    if (blocks > 0x7fffffffLL) return false;
+    auto kern = k_sweep_box<D_, M_, BY, BZ>;
+    *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (*err != cudaSuccess) return true;
+    kern<<<(unsigned)blocks, C::NT, C::SMEM, st>>>(nx, ny, nz, np, ntx, nty, ntz, wsrc, vals, g, out, c2, mu, clip);
+    *err = cudaGetLastError();
+    return true;
+}
+
 // One thread per (phase, direction, voxel): three passes over the window
 // (minimum distance, unnormalised weights, normalisation).
 __global__ void k_weights(int nx, int ny, int nz, int np, const float *__restrict__ a, int d, int M, float c2,
@@ -219,13 +449,30 @@ static float exponent_scale(float h)
 tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
                          float *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
 {
+    const float c2 = exponent_scale(h);
+    cudaError_t err = cudaSuccess;
+    bool done = false;
+    if (d == 1 && M == 1) done = launch_box<1, 1>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    else if (d == 1 && M == 2) done = launch_box<1, 2>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    else if (d == 1 && M == 3) done = launch_box<1, 3>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 1) done = launch_box<2, 1>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 2) done = launch_box<2, 2>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 3) done = launch_box<2, 3>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, &err);
+    if (done) {
+        if (err != cudaSuccess) {
+            set_error("box-sum sweep launch failed: %s", cudaGetErrorString(err));
+            return TNLM_ERR_CUDA;
+        }
+        return TNLM_OK;
+    }
+    // other (d, M): generic tiled kernel with direct patch sums
     const int ntz = (nz + kTZ - 1) / kTZ;
     dim3 block(kTX, kTY, kTZ);
     dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, np * ntz);
     const size_t smem = sweep_smem(d, M);
     if (smem > 48 * 1024)
         TNLM_TRY_CUDA(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sweep<<<grid, block, smem, st>>>(nx, ny, nz, np, ntz, wsrc, vals, g, out, d, M, exponent_scale(h), mu, clip);
+    k_sweep<<<grid, block, smem, st>>>(nx, ny, nz, np, ntz, wsrc, vals, g, out, d, M, c2, mu, clip);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
 }
