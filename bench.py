@@ -21,6 +21,7 @@ prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -124,12 +125,20 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Slowest rank's value (the job ends when the last rank does)."""
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(steps: int, world: int, ms_max: float) -> float:
+    """Whole-job FBS iterations/s: every rank runs `steps` iterations of its own
+    reconstruction; the job takes the slowest rank's time."""
+    return steps * world / (ms_max / 1e3)
 
 
 # ---------------------------------------------------------------------------
@@ -169,11 +178,13 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     tnlm.build()
     cfg = synth.C2
+    if args.phases != cfg.n_phases:  # smaller case of the same kernels (profiling captures)
+        cfg = dataclasses.replace(cfg, n_phases=args.phases)
     pb = synth.recon_problem(cfg, device="cuda")  # same seeded problem on every rank
     geom = tnlm.Geometry(pb.geom)
     y = pb.y.contiguous()
     x0 = torch.from_numpy(synth.uniform(geom.vol_shape, 2024)).cuda()
-    L = tnlm.tnlm_operator_norm(geom, x0, 20)
+    L = tnlm.tnlm_operator_norm(geom, x0, args.power_iters)
     tau = 1.0 / L
     params = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=1, n_inner=1, clip_nonneg=1)
     f = torch.zeros(geom.vol_shape, device="cuda")
@@ -201,7 +212,7 @@ def run_ours(args, rank, world, local):
     stage_ms, stage_n = geom.stage_timing()
     geom.set_stage_timing(False)
     ms_max = max_over_ranks(ms_total, world)
-    value = args.steps * world / (ms_max / 1e3)
+    value = job_throughput(args.steps, world, ms_max)
 
     # end to end through the public API with host buffers
     y_host = y.cpu().pin_memory()
@@ -260,6 +271,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
     }
+    if args.phases != 10:
+        line["config"]["workload"] += f" [reduced to {args.phases} phases]"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(cfg, pb)
     return line
@@ -334,6 +347,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", type=int, default=10, help="phases of the workload (10; fewer for profiling)")
+    ap.add_argument("--power-iters", type=int, default=20, help="power iterations that size the step tau")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
