@@ -45,7 +45,12 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
 # each kernel on this workload, with the SHA-256 of the kernel source it was
 # measured on; a changed source invalidates the figure (reported as null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload
+    "k_forward": {"bytes_per_launch": int((272.267776e6 + 147.883008e6) * 10 / 6), "source_sha": "0ad0d5313e057fc5"},
+    "k_backproject": {"bytes_per_launch": int((256.100608e6 + 84.198656e6) * 10 / 6), "source_sha": "0ad0d5313e057fc5"},
+    "k_sweep": {"bytes_per_launch": int((161.4336e6 + 83.991808e6) * 10 / 6), "source_sha": "c52872dcd2f275b9"},
+}
 
 
 def _src_sha(fname: str) -> str:
