@@ -159,100 +159,148 @@ __device__ __forceinline__ float xbox(float b)
     }
 }
 
-template <int D_, int M_, int BY, int BZ, bool INTERIOR>
-__device__ __forceinline__ void box_direction(const float (&ai)[BY + 2 * D_][BZ + 2 * D_], const float *s_aj,
-                                              const float *s_vj, int lane, int wy, int wz, int x, int yb, int zb,
-                                              int nx, int ny, int nz, float c2, float (&res)[BY][BZ])
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d)
 {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// x box sum over the warp lanes of a pair of values (two y rows)
+template <int D_>
+__device__ __forceinline__ float2 xbox2(float2 b)
+{
+    if constexpr (D_ == 0) {
+        return b;
+    } else if constexpr (D_ == 1) {
+        return __fadd2_rn(__fadd2_rn(shfl_up2(b, 1), b), shfl_down2(b, 1));
+    } else if constexpr (D_ == 2) {
+        const float2 p = __fadd2_rn(b, shfl_down2(b, 1));  // b(x) + b(x+1)
+        return __fadd2_rn(__fadd2_rn(shfl_up2(p, 2), p), shfl_down2(b, 2));
+    } else {
+        float2 acc = b;
+#pragma unroll
+        for (int t = 1; t <= D_; ++t) acc = __fadd2_rn(acc, __fadd2_rn(shfl_up2(b, t), shfl_down2(b, t)));
+        return acc;
+    }
+}
+
+// One direction of the sweep for this thread's 2 x BZ outputs (y rows j = 0, 1
+// are processed as FP32x2 pairs).  ai holds the thread's patch block of phase
+// i as [z][y pair]; res accumulates N/Z per output.
+template <int D_, int M_, int BZ, bool INTERIOR>
+__device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2 + 2 * D_) / 2], const float *s_aj,
+                                              const float *s_vj, int lane, int wy, int wz, int x, int yb, int zb,
+                                              int nx, int ny, int nz, float c2, float2 (&res)[BZ])
+{
+    constexpr int BY = 2;
     using C = BoxCfg<D_, M_, BY, BZ>;
-    float mref[BY][BZ], N[BY][BZ], Z[BY][BZ];
+    constexpr int SP = C::SY / 2;  // y pairs of the patch block
+    float2 mref[BZ], N[BZ], Z[BZ];
 #pragma unroll
-    for (int j = 0; j < BY; ++j)
-#pragma unroll
-        for (int k = 0; k < BZ; ++k) {
-            mref[j][k] = FLT_MAX;
-            N[j][k] = 0.f;
-            Z[j][k] = 0.f;
-        }
+    for (int k = 0; k < BZ; ++k) {
+        mref[k] = make_float2(FLT_MAX, FLT_MAX);
+        N[k] = make_float2(0.f, 0.f);
+        Z[k] = make_float2(0.f, 0.f);
+    }
+    const float2 nc2 = make_float2(-c2, -c2);
     for (int dy = -M_; dy <= M_; ++dy) {
-        bool vy[BY];
-#pragma unroll
-        for (int j = 0; j < BY; ++j) vy[j] = INTERIOR || (unsigned)(yb + j + dy) < (unsigned)ny;
+        const bool vy0 = INTERIOR || (unsigned)(yb + dy) < (unsigned)ny;
+        const bool vy1 = INTERIOR || (unsigned)(yb + 1 + dy) < (unsigned)ny;
         for (int dx = -M_; dx <= M_; ++dx) {
             const bool vx = INTERIOR || (unsigned)(x + dx) < (unsigned)nx;
-            // neighbour-phase values along z for this (dy, dx): a sliding window of SZ rows
+            const bool vxy0 = vx && vy0, vxy1 = vx && vy1;
             const float *paj = s_aj + (wy * BY + dy + M_) * C::AJX + lane + dx + M_;
             const float *pvj = s_vj + (wy * BY + dy + M_) * C::VJX + lane + dx + M_;
-            float aw[2 * M_ + C::SZ][C::SY];
-            float vw[2 * M_ + BZ][BY];
+            // neighbour-phase rows along z, a sliding window of SZ rows of y pairs
+            float2 aw[2 * M_ + C::SZ][SP];
+            float2 vw[2 * M_ + BZ];
 #pragma unroll
             for (int r = 0; r < C::SZ - 1; ++r)
 #pragma unroll
-                for (int yy = 0; yy < C::SY; ++yy) aw[r][yy] = paj[((wz * BZ + r) * C::AJY + yy) * C::AJX];
+                for (int p = 0; p < SP; ++p) {
+                    const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
+                    aw[r][p] = make_float2(q0[0], q0[C::AJX]);
+                }
 #pragma unroll
-            for (int r = 0; r < BZ - 1; ++r)
-#pragma unroll
-                for (int j = 0; j < BY; ++j) vw[r][j] = pvj[((wz * BZ + r) * C::VJY + j) * C::VJX];
+            for (int r = 0; r < BZ - 1; ++r) {
+                const float *q0 = pvj + (wz * BZ + r) * C::VJY * C::VJX;
+                vw[r] = make_float2(q0[0], q0[C::VJX]);
+            }
 #pragma unroll
             for (int q = 0; q <= 2 * M_; ++q) {  // q = dz + M
                 {
                     const int r = q + C::SZ - 1;
 #pragma unroll
-                    for (int yy = 0; yy < C::SY; ++yy) aw[r][yy] = paj[((wz * BZ + r) * C::AJY + yy) * C::AJX];
+                    for (int p = 0; p < SP; ++p) {
+                        const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
+                        aw[r][p] = make_float2(q0[0], q0[C::AJX]);
+                    }
                     const int rv = q + BZ - 1;
-#pragma unroll
-                    for (int j = 0; j < BY; ++j) vw[rv][j] = pvj[((wz * BZ + rv) * C::VJY + j) * C::VJX];
+                    const float *q1 = pvj + (wz * BZ + rv) * C::VJY * C::VJX;
+                    vw[rv] = make_float2(q1[0], q1[C::VJX]);
                 }
-                // z box sums of the squared differences, row by row
-                float bz[C::SY][BZ];
+                // squared differences and z box sums, per y pair
+                float2 bz[BZ][SP];
 #pragma unroll
-                for (int yy = 0; yy < C::SY; ++yy) {
-                    float srow[C::SZ];
+                for (int p = 0; p < SP; ++p) {
+                    float2 sq[C::SZ];
 #pragma unroll
                     for (int zz = 0; zz < C::SZ; ++zz) {
-                        const float t = ai[yy][zz] - aw[q + zz][yy];
-                        srow[zz] = t * t;
+                        const float2 t = __fadd2_rn(ai[zz][p], make_float2(-aw[q + zz][p].x, -aw[q + zz][p].y));
+                        sq[zz] = __fmul2_rn(t, t);
                     }
 #pragma unroll
                     for (int k = 0; k < BZ; ++k) {
-                        float acc = srow[k];
+                        float2 acc = sq[k];
 #pragma unroll
-                        for (int t = 1; t <= 2 * D_; ++t) acc += srow[k + t];
-                        bz[yy][k] = acc;
+                        for (int t = 1; t <= 2 * D_; ++t) acc = __fadd2_rn(acc, sq[k + t]);
+                        bz[k][p] = acc;
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < BY; ++j)
+                for (int k = 0; k < BZ; ++k) {
+                    // y box sums of the two output rows: row 0 sums y 0..2d, row 1 sums y 1..2d+1,
+                    // both direct sums sharing the middle rows m = y 1..2d
+                    float m = bz[k][0].y;
 #pragma unroll
-                    for (int k = 0; k < BZ; ++k) {
-                        float acc = bz[j][k];
-#pragma unroll
-                        for (int t = 1; t <= 2 * D_; ++t) acc += bz[j + t][k];
-                        const float Dv = xbox<D_>(acc);  // patch distance of output (j, k) at this offset
-                        const bool valid = INTERIOR || (vx && vy[j] && (unsigned)(zb + k + q - M_) < (unsigned)nz);
-                        if (valid) {
-                            const float a = fmaf(-Dv, c2, mref[j][k]);  // log2 weight vs the reference
-                            float e;
-                            if (a > kRescale) {  // candidate beats the reference by 2^kRescale: move it
-                                const float sc = ex2(-a);
-                                N[j][k] *= sc;
-                                Z[j][k] *= sc;
-                                mref[j][k] = Dv * c2;
-                                e = 1.f;
-                            } else {
-                                e = ex2(a);
-                            }
-                            N[j][k] = fmaf(e, vw[q + k][j], N[j][k]);
-                            Z[j][k] += e;
-                        }
+                    for (int yy = 2; yy <= 2 * D_; ++yy) m += (yy & 1) ? bz[k][yy / 2].y : bz[k][yy / 2].x;
+                    const float2 yb2 = make_float2(bz[k][0].x + m, m + bz[k][SP - 1].y);
+                    const float2 Dv = xbox2<D_>(yb2);  // patch distances of outputs (0,k) and (1,k)
+                    float2 a = __ffma2_rn(Dv, nc2, mref[k]);  // log2 weights vs the references
+                    const bool vz = INTERIOR || (unsigned)(zb + k + q - M_) < (unsigned)nz;
+                    if (!INTERIOR) {
+                        if (!(vxy0 && vz)) a.x = -FLT_MAX;
+                        if (!(vxy1 && vz)) a.y = -FLT_MAX;
                     }
+                    if (a.x > kRescale) {  // candidate beats the reference by 2^kRescale: move it
+                        const float sc = ex2(-a.x);
+                        N[k].x *= sc;
+                        Z[k].x *= sc;
+                        mref[k].x = Dv.x * c2;
+                        a.x = 0.f;
+                    }
+                    if (a.y > kRescale) {
+                        const float sc = ex2(-a.y);
+                        N[k].y *= sc;
+                        Z[k].y *= sc;
+                        mref[k].y = Dv.y * c2;
+                        a.y = 0.f;
+                    }
+                    const float2 e = make_float2(ex2(a.x), ex2(a.y));
+                    N[k] = __ffma2_rn(e, vw[q + k], N[k]);
+                    Z[k] = __fadd2_rn(Z[k], e);
+                }
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < BY; ++j)
-#pragma unroll
-        for (int k = 0; k < BZ; ++k) res[j][k] += N[j][k] / Z[j][k];
+    for (int k = 0; k < BZ; ++k) {
+        res[k].x += N[k].x / Z[k].x;
+        res[k].y += N[k].y / Z[k].y;
+    }
 }
 
 template <int D_, int M_, int BY, int BZ>
@@ -281,22 +329,23 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
     const bool interior = X0 - M_ >= 0 && X0 + C::TXO - 1 + M_ < nx && Y0 - M_ >= 0 && Y0 + C::TY - 1 + M_ < ny &&
                           Z0 - M_ >= 0 && Z0 + C::TZ - 1 + M_ < nz;
 
-    // this thread's patch block of phase i (clamped reads), kept for all offsets
-    float ai[C::SY][C::SZ];
+    // this thread's patch block of phase i (clamped reads) as [z][y pair], kept for all offsets
+    float2 ai[C::SZ][C::SY / 2];
     {
         const float *src = wsrc + i * nvox;
         const int cx = clampi(x, nx);
 #pragma unroll
-        for (int yy = 0; yy < C::SY; ++yy)
+        for (int zz = 0; zz < C::SZ; ++zz)
 #pragma unroll
-            for (int zz = 0; zz < C::SZ; ++zz)
-                ai[yy][zz] = __ldg(src + ((long long)clampi(zb - D_ + zz, nz) * ny + clampi(yb - D_ + yy, ny)) * nx + cx);
+            for (int p = 0; p < C::SY / 2; ++p) {
+                const long long zo = (long long)clampi(zb - D_ + zz, nz) * ny;
+                ai[zz][p] = make_float2(__ldg(src + (zo + clampi(yb - D_ + 2 * p, ny)) * nx + cx),
+                                        __ldg(src + (zo + clampi(yb - D_ + 2 * p + 1, ny)) * nx + cx));
+            }
     }
-    float res[BY][BZ];
+    float2 res[BZ];
 #pragma unroll
-    for (int j = 0; j < BY; ++j)
-#pragma unroll
-        for (int k = 0; k < BZ; ++k) res[j][k] = 0.f;
+    for (int k = 0; k < BZ; ++k) res[k] = make_float2(0.f, 0.f);
 
     for (int dir = 0; dir < 2; ++dir) {
         const int jp = dir == 0 ? (i + 1) % np : (i - 1 + np) % np;
@@ -307,9 +356,9 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
                       C::NT);
         __syncthreads();
         if (interior)
-            box_direction<D_, M_, BY, BZ, true>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
+            box_direction<D_, M_, BZ, true>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
         else
-            box_direction<D_, M_, BY, BZ, false>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
+            box_direction<D_, M_, BZ, false>(ai, s_aj, s_vj, lane, wy, wz, x, yb, zb, nx, ny, nz, c2, res);
     }
     if (lane >= D_ && lane < 32 - D_ && x < nx) {
         const float inv = 1.f / (2.f + mu);
@@ -320,8 +369,9 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
                 const int y = yb + j, z = zb + k;
                 if (y < ny && z < nz) {
                     const long long o = i * nvox + ((long long)z * ny + y) * nx + x;
-                    float f = (mu * __ldg(g + o) + res[j][k]) * inv;  // Eq. 8
-                    if (clip) f = fmaxf(f, 0.f);                     // positivity (TNLM-R step 4)
+                    const float r = j == 0 ? res[k].x : res[k].y;
+                    float f = (mu * __ldg(g + o) + r) * inv;  // Eq. 8
+                    if (clip) f = fmaxf(f, 0.f);              // positivity (TNLM-R step 4)
                     out[o] = f;
                 }
             }
