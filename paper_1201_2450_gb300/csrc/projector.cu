@@ -162,14 +162,17 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
                   const float *__restrict__ proj, const float *vin, float *vout, float alpha, float beta,
                   int nchunks)
 {
-    extern __shared__ float sm[];
-    float *s_v = sm;          // v coordinate of each detector row
-    float *s_iv = sm + G.nv;  // its reciprocal (0 for v == 0)
-    for (int t = threadIdx.y * kBpBX + threadIdx.x; t < G.nv; t += kBpBX * kBpBY) {
+    constexpr int NT = kBpBX * kBpBY;
+    extern __shared__ float4 sm4[];
+    float4 *s_row = sm4;                                // per detector row: (v, 1/v or 0, v^2, 0)
+    float *s_acc = reinterpret_cast<float *>(sm4 + G.nv);  // [kBpCH][NT] per-thread accumulators
+    const int tid = threadIdx.y * kBpBX + threadIdx.x;
+    for (int t = tid; t < G.nv; t += NT) {
         const float v = ((float)t - G.vc) * G.dv + G.v_off;
-        s_v[t] = v;
-        s_iv[t] = v != 0.f ? 1.0f / v : 0.f;
+        s_row[t] = make_float4(v, v != 0.f ? 1.0f / v : 0.f, v * v, 0.f);
     }
+#pragma unroll
+    for (int k = 0; k < kBpCH; ++k) s_acc[k * NT + tid] = 0.f;
     __syncthreads();
     const int ix = blockIdx.x * kBpBX + threadIdx.x;
     const int iy = blockIdx.y * kBpBY + threadIdx.y;
@@ -179,9 +182,7 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
     const int nzc = min(kBpCH, G.nz - iz0);
     const float xc = G.b0x + ((float)ix + 0.5f) * G.dx;
     const float yc = G.b0y + ((float)iy + 0.5f) * G.dy;
-    float acc[kBpCH];
-#pragma unroll
-    for (int k = 0; k < kBpCH; ++k) acc[k] = 0.f;
+    const float fvscale = G.inv_dv, fvoff = G.vc - G.v_off * G.inv_dv;  // row coordinate of v: v*fvscale + fvoff
 
     const int v_end = view_off[phase + 1];
     for (int vg = view_off[phase]; vg < v_end; ++vg) {
@@ -217,54 +218,69 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
             slab_local(qy, gy, G.hy, glo, ghi, ok);
             if (!ok || !(glo < ghi)) continue;
             const float ialo = 1.0f / (ac + glo), iahi = 1.0f / (ac + ghi);
+            const float dg = ghi - glo;  // xy chord of this pixel column (ray-parameter units)
             const float len_u2 = G.sdd * G.sdd + u * u;
-#pragma unroll
-            for (int k = 0; k < kBpCH; ++k) {
-                if (k < nzc) {
-                    const float zc = G.b0z + ((float)(iz0 + k) + 0.5f) * G.dz;
-                    const float zlo = zc - G.hz, zhi = zc + G.hz;
-                    // detector rows whose rays can meet the cell: v = z / alpha over its z and alpha ranges
-                    const float vmin = fminf(zlo * ialo, zlo * iahi);
-                    const float vmax = fmaxf(zhi * ialo, zhi * iahi);
-                    const float fv_lo = fmaxf((vmin - G.v_off) * G.inv_dv + G.vc - 1e-3f, -1.f);
-                    const float fv_hi = fminf((vmax - G.v_off) * G.inv_dv + G.vc + 1e-3f, (float)G.nv);
-                    const int iv_lo = max(0, (int)ceilf(fv_lo));
-                    const int iv_hi = min(G.nv - 1, (int)floorf(fv_hi));
-                    float sacc = 0.f;
-                    for (int iv = iv_lo; iv <= iv_hi; ++iv) {
-                        const float v = s_v[iv];
-                        float zl, zh;
-                        if (v != 0.f) {
-                            const float oz = ac * v - zc;  // z offset of the ray from the cell centre at gamma 0
-                            const float t0 = (-G.hz - oz) * s_iv[iv];
-                            const float t1 = (G.hz - oz) * s_iv[iv];
-                            zl = fminf(t0, t1);
-                            zh = fmaxf(t0, t1);
-                        } else {
-                            const bool in = (zlo <= 0.f) && (0.f < zhi);
-                            zl = in ? -FLT_MAX : FLT_MAX;
-                            zh = in ? FLT_MAX : -FLT_MAX;
-                        }
-                        const float seg = fminf(ghi, zh) - fmaxf(glo, zl);
-                        if (seg > 0.f) {
-                            float r = __ldg(pv + iv * G.nu + iu);
-                            if (!SCALED) r *= sqrtf(len_u2 + v * v);
-                            sacc = fmaf(r, seg, sacc);
-                        }
-                    }
-                    acc[k] += sacc;
+            const float *__restrict__ pc = pv + iu;
+            for (int k = 0; k < nzc; ++k) {
+                const float zc = G.b0z + ((float)(iz0 + k) + 0.5f) * G.dz;
+                const float zlo = zc - G.hz, zhi = zc + G.hz;
+                // rows whose rays can meet the cell (v = z / alpha over its z and alpha ranges) ...
+                const float vmin = fminf(zlo * ialo, zlo * iahi);
+                const float vmax = fmaxf(zhi * ialo, zhi * iahi);
+                // ... and rows whose ray stays inside the cell's z slab over the whole xy chord
+                const float vflo = fmaxf(zlo * ialo, zlo * iahi);
+                const float vfhi = fminf(zhi * ialo, zhi * iahi);
+                const int iv_lo = max(0, (int)ceilf(fmaxf(fmaf(vmin, fvscale, fvoff) - 1e-3f, -1.f)));
+                const int iv_hi = min(G.nv - 1, (int)floorf(fminf(fmaf(vmax, fvscale, fvoff) + 1e-3f, (float)G.nv)));
+                int if_lo = max(iv_lo, (int)ceilf(fmaxf(fmaf(vflo, fvscale, fvoff) + 1e-3f, -1.f)));
+                int if_hi = min(iv_hi, (int)floorf(fminf(fmaf(vfhi, fvscale, fvoff) - 1e-3f, (float)G.nv)));
+                if (if_lo > if_hi) {  // no full row: every candidate row is partial
+                    if_lo = iv_hi + 1;
+                    if_hi = iv_hi;
                 }
+                // full rows: the exact chord is the whole xy chord dg
+                float sfull = 0.f;
+                for (int iv = if_lo; iv <= if_hi; ++iv) {
+                    float r = __ldg(pc + iv * G.nu);
+                    if (!SCALED) r *= sqrtf(len_u2 + s_row[iv].z);
+                    sfull += r;
+                }
+                // partial rows (below and above the full range): exact z-slab test
+                float spart = 0.f;
+                for (int iv = iv_lo; iv <= iv_hi; ++iv) {
+                    if (iv == if_lo) {  // skip the full range
+                        iv = if_hi;
+                        continue;
+                    }
+                    const float4 rw = s_row[iv];
+                    float zl, zh;
+                    if (rw.x != 0.f) {
+                        const float oz = fmaf(ac, rw.x, -zc);  // z offset of the ray from the cell centre at gamma 0
+                        const float t0 = (-G.hz - oz) * rw.y;
+                        const float t1 = (G.hz - oz) * rw.y;
+                        zl = fminf(t0, t1);
+                        zh = fmaxf(t0, t1);
+                    } else {  // ray in the plane z = 0: inside iff zlo <= 0 < zhi
+                        const bool in = (zlo <= 0.f) && (0.f < zhi);
+                        zl = in ? -FLT_MAX : FLT_MAX;
+                        zh = in ? FLT_MAX : -FLT_MAX;
+                    }
+                    const float seg = fminf(ghi, zh) - fmaxf(glo, zl);
+                    if (seg > 0.f) {
+                        float r = __ldg(pc + iv * G.nu);
+                        if (!SCALED) r *= sqrtf(len_u2 + rw.z);
+                        spart = fmaf(r, seg, spart);
+                    }
+                }
+                s_acc[k * NT + tid] += fmaf(sfull, dg, spart);
             }
         }
     }
     const long long base = (long long)phase * G.nvox + ((long long)iz0 * G.ny + iy) * G.nx + ix;
-#pragma unroll
-    for (int k = 0; k < kBpCH; ++k) {
-        if (k < nzc) {
-            const long long o = base + (long long)k * G.nx * G.ny;
-            const float bp = alpha * acc[k];
-            vout[o] = beta != 0.f ? fmaf(beta, vin[o], bp) : bp;
-        }
+    for (int k = 0; k < nzc; ++k) {
+        const long long o = base + (long long)k * G.nx * G.ny;
+        const float bp = alpha * s_acc[k * NT + tid];
+        vout[o] = beta != 0.f ? fmaf(beta, vin[o], bp) : bp;
     }
 }
 
@@ -295,7 +311,11 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
     const int nchunks = (kg.nz + kBpCH - 1) / kBpCH;
     dim3 block(kBpBX, kBpBY);
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchunks);
-    const size_t smem = 2 * sizeof(float) * kg.nv;
+    const size_t smem = sizeof(float4) * kg.nv + sizeof(float) * kBpCH * kBpBX * kBpBY;
+    if (smem > 48 * 1024) {
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     if (scaled)
         k_backproject<true><<<grid, block, smem, st>>>(kg, views, view_off, proj, vin, vout, alpha, beta, nchunks);
     else
