@@ -100,43 +100,78 @@ __global__ void __launch_bounds__(kFwdBX *kFwdBY)
         slab_grid(Ez, Gz, G.nz, blo, bhi, ok);
         float acc = 0.f;
         if (ok && blo < bhi) {
-            int ix = clamp_floor(fmaf(blo, Gx, Ex), G.nx);
-            int iy = clamp_floor(fmaf(blo, Gy, Ey), G.ny);
-            int iz = clamp_floor(fmaf(blo, Gz, Ez), G.nz);
-            const int sx = Gx > 0.f ? 1 : -1, sy = Gy > 0.f ? 1 : -1, sz = Gz > 0.f ? 1 : -1;
-            const float ivx = Gx != 0.f ? 1.0f / Gx : 0.f;
-            const float ivy = Gy != 0.f ? 1.0f / Gy : 0.f;
-            const float ivz = Gz != 0.f ? 1.0f / Gz : 0.f;
-            // parameter of the next plane crossing on each axis, recomputed from the index every step
-            float bx = Gx != 0.f ? ((float)(ix + (sx > 0)) - Ex) * ivx : FLT_MAX;
-            float by = Gy != 0.f ? ((float)(iy + (sy > 0)) - Ey) * ivy : FLT_MAX;
-            float bz = Gz != 0.f ? ((float)(iz + (sz > 0)) - Ez) * ivz : FLT_MAX;
-            const float *__restrict__ fp = vol + (long long)V.phase * G.nvox;
-            int idx = (iz * G.ny + iy) * G.nx + ix;
+            // Axis roles: a = the dominant of x, y (z if steeper than both), b = the other in-plane
+            // axis, c = the remaining one (z for every ray of a practical cone).  A slab between two
+            // a-planes holds at most one b crossing (|Gb| <= |Ga|), taken without branching; c
+            // crossings depend only on the detector row, so the lanes of a warp (one row, adjacent
+            // columns) cross c planes together and the branch for them stays coherent.
+            const float ax = fabsf(Gx), ay = fabsf(Gy), az = fabsf(Gz);
+            const bool zdom = az > ax && az > ay;
+            const bool xa = !zdom && ax >= ay;  // x dominant: (a,b,c) = (x,y,z); y dominant: (y,x,z)
             const int sxy = G.nx * G.ny;
+            const float Ea = zdom ? Ez : (xa ? Ex : Ey), Eb = xa ? Ey : Ex, Ec = zdom ? Ey : Ez;
+            const float Ga = zdom ? Gz : (xa ? Gx : Gy), Gb = xa ? Gy : Gx, Gc = zdom ? Gy : Gz;
+            const int na = zdom ? G.nz : (xa ? G.nx : G.ny), nb = xa ? G.ny : G.nx, nc = zdom ? G.ny : G.nz;
+            const int ta = zdom ? sxy : (xa ? 1 : G.nx), tb = xa ? G.nx : 1, tc = zdom ? G.nx : sxy;
+            const int sa = Ga > 0.f ? 1 : -1, sb = Gb > 0.f ? 1 : -1, sc = Gc > 0.f ? 1 : -1;
+            const int pa = Ga > 0.f, pb = Gb > 0.f, pc = Gc > 0.f;
+            const float iva = 1.0f / Ga;
+            const float ivb = Gb != 0.f ? 1.0f / Gb : 0.f;
+            const float ivc = Gc != 0.f ? 1.0f / Gc : 0.f;
+            int ia = clamp_floor(fmaf(blo, Ga, Ea), na);
+            int ib = clamp_floor(fmaf(blo, Gb, Eb), nb);
+            int ic = clamp_floor(fmaf(blo, Gc, Ec), nc);
+            // next plane crossing on each axis, in the same form as the entry/exit test above so
+            // that exit planes compare equal to bhi
+            float ba = ((float)(ia + pa) - Ea) * iva;
+            float bb = Gb != 0.f ? ((float)(ib + pb) - Eb) * ivb : FLT_MAX;
+            float bc = Gc != 0.f ? ((float)(ic + pc) - Ec) * ivc : FLT_MAX;
+            const float *__restrict__ fp = vol + (long long)V.phase * G.nvox;
+            int idx = ia * ta + ib * tb + ic * tc;
+            float fcur = __ldg(fp + idx);
             float bcur = blo;
-            const int maxit = G.nx + G.ny + G.nz + 3;
-            for (int it = 0; it < maxit; ++it) {
-                const float bn = fminf(fminf(bx, by), fminf(bz, bhi));
-                acc = fmaf(__ldg(fp + idx), fmaxf(bn - bcur, 0.f), acc);
-                bcur = bn;
-                if (bn >= bhi) break;
-                if (bn == bx) {
-                    ix += sx;
-                    if ((unsigned)ix >= (unsigned)G.nx) break;
-                    idx += sx;
-                    bx = ((float)(ix + (sx > 0)) - Ex) * ivx;
-                } else if (bn == by) {
-                    iy += sy;
-                    if ((unsigned)iy >= (unsigned)G.ny) break;
-                    idx += sy * G.nx;
-                    by = ((float)(iy + (sy > 0)) - Ey) * ivy;
-                } else {
-                    iz += sz;
-                    if ((unsigned)iz >= (unsigned)G.nz) break;
-                    idx += sz * sxy;
-                    bz = ((float)(iz + (sz > 0)) - Ez) * ivz;
+            bool done = false;
+            for (int it = 0; it <= na && !done; ++it) {
+                const float bend = fminf(ba, bhi);  // end of this a-slab inside the volume
+                for (int rc = 0; rc < 4 && bc < bend; ++rc) {  // c crossings (coherent, rare)
+                    if (bb < bc) {
+                        acc = fmaf(fcur, fmaxf(bb - bcur, 0.f), acc);
+                        bcur = bb;
+                        ib += sb;
+                        idx += sb * tb;
+                        fcur = (unsigned)ib < (unsigned)nb ? __ldg(fp + idx) : 0.f;
+                        bb = ((float)(ib + pb) - Eb) * ivb;
+                    }
+                    acc = fmaf(fcur, fmaxf(bc - bcur, 0.f), acc);
+                    bcur = bc;
+                    ic += sc;
+                    if ((unsigned)ic >= (unsigned)nc || (unsigned)ib >= (unsigned)nb) {
+                        done = true;
+                        break;
+                    }
+                    idx += sc * tc;
+                    fcur = __ldg(fp + idx);
+                    bc = ((float)(ic + pc) - Ec) * ivc;
                 }
+                if (done) break;
+                // at most one b crossing in the rest of the slab
+                const bool hit = bb < bend;
+                const float e1 = hit ? bb : bend;
+                acc = fmaf(fcur, fmaxf(e1 - bcur, 0.f), acc);
+                if (hit) {
+                    ib += sb;
+                    idx += sb * tb;
+                    fcur = (unsigned)ib < (unsigned)nb ? __ldg(fp + idx) : 0.f;
+                    bb = ((float)(ib + pb) - Eb) * ivb;
+                }
+                acc = fmaf(fcur, bend - e1, acc);
+                bcur = bend;
+                if (bend >= bhi || (unsigned)ib >= (unsigned)nb) break;
+                ia += sa;
+                if ((unsigned)ia >= (unsigned)na) break;
+                idx += sa * ta;
+                fcur = __ldg(fp + idx);
+                ba = ((float)(ia + pa) - Ea) * iva;
             }
             acc *= len;
         }
@@ -221,19 +256,28 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
             const float dg = ghi - glo;  // xy chord of this pixel column (ray-parameter units)
             const float len_u2 = G.sdd * G.sdd + u * u;
             const float *__restrict__ pc = pv + iu;
+            // Row coordinate of the image of a z boundary seen at the near / far end of the xy chord:
+            // row = z * (1/alpha) / dv + (vc - v_off/dv).  Adjacent cells share a boundary, so each
+            // boundary is mapped once and carried to the next cell.
+            const float sra = ialo * fvscale, srb = iahi * fvscale;
+            float zb = fmaf((float)iz0, G.dz, G.b0z);
+            float pa = fmaf(zb, sra, fvoff), pb = fmaf(zb, srb, fvoff);
+            float rlo = fminf(pa, pb), rhi = fmaxf(pa, pb);
             for (int k = 0; k < nzc; ++k) {
-                const float zc = G.b0z + ((float)(iz0 + k) + 0.5f) * G.dz;
+                const float zc = fmaf((float)(iz0 + k) + 0.5f, G.dz, G.b0z);
                 const float zlo = zc - G.hz, zhi = zc + G.hz;
-                // rows whose rays can meet the cell (v = z / alpha over its z and alpha ranges) ...
-                const float vmin = fminf(zlo * ialo, zlo * iahi);
-                const float vmax = fmaxf(zhi * ialo, zhi * iahi);
-                // ... and rows whose ray stays inside the cell's z slab over the whole xy chord
-                const float vflo = fmaxf(zlo * ialo, zlo * iahi);
-                const float vfhi = fminf(zhi * ialo, zhi * iahi);
-                const int iv_lo = max(0, (int)ceilf(fmaxf(fmaf(vmin, fvscale, fvoff) - 1e-3f, -1.f)));
-                const int iv_hi = min(G.nv - 1, (int)floorf(fminf(fmaf(vmax, fvscale, fvoff) + 1e-3f, (float)G.nv)));
-                int if_lo = max(iv_lo, (int)ceilf(fmaxf(fmaf(vflo, fvscale, fvoff) + 1e-3f, -1.f)));
-                int if_hi = min(iv_hi, (int)floorf(fminf(fmaf(vfhi, fvscale, fvoff) - 1e-3f, (float)G.nv)));
+                zb = fmaf((float)(iz0 + k + 1), G.dz, G.b0z);
+                pa = fmaf(zb, sra, fvoff);
+                pb = fmaf(zb, srb, fvoff);
+                const float rlo2 = fminf(pa, pb), rhi2 = fmaxf(pa, pb);
+                // candidate rows meet the cell somewhere; full rows stay inside its z slab over the whole
+                // xy chord (both with a 1e-3-row safety margin; the exact test decides the rest)
+                const int iv_lo = max(0, __float2int_ru(fmaxf(rlo - 1e-3f, -1.f)));
+                const int iv_hi = min(G.nv - 1, __float2int_rd(fminf(rhi2 + 1e-3f, (float)G.nv)));
+                int if_lo = max(iv_lo, __float2int_ru(fmaxf(rhi + 1e-3f, -1.f)));
+                int if_hi = min(iv_hi, __float2int_rd(fminf(rlo2 - 1e-3f, (float)G.nv)));
+                rlo = rlo2;
+                rhi = rhi2;
                 if (if_lo > if_hi) {  // no full row: every candidate row is partial
                     if_lo = iv_hi + 1;
                     if_hi = iv_hi;
