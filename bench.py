@@ -160,6 +160,59 @@ def algorithmic_bytes(cfg, n_views_total):
     }
 
 
+def projection_nnz(desc: dict, device="cuda") -> int:
+    """Non-zeros of P: the number of (ray, cell) pairs with a positive chord,
+    i.e. cells crossed per ray = 1 + sum over axes of |exit cell - entry cell|
+    (FP64, counted view by view on the device)."""
+    nu, nv = desc["nu"], desc["nv"]
+    dev = torch.device(device)
+    u = (torch.arange(nu, device=dev, dtype=torch.float64) - 0.5 * (nu - 1)) * desc["du"] + desc["u_off"]
+    v = (torch.arange(nv, device=dev, dtype=torch.float64) - 0.5 * (nv - 1)) * desc["dv"] + desc["v_off"]
+    V, U = torch.meshgrid(v, u, indexing="ij")
+    n = [desc["nx"], desc["ny"], desc["nz"]]
+    w = [desc["dx"], desc["dy"], desc["dz"]]
+    b0 = [desc["cx"] - 0.5 * n[0] * w[0], desc["cy"] - 0.5 * n[1] * w[1], desc["cz"] - 0.5 * n[2] * w[2]]
+    total = 0
+    for th in desc["angles"]:
+        c, s_ = float(np.cos(th)), float(np.sin(th))
+        src = [desc["sad"] * c, desc["sad"] * s_, 0.0]
+        pix = [(desc["sad"] - desc["sdd"]) * c - U * s_, (desc["sad"] - desc["sdd"]) * s_ + U * c, V]
+        d = [pix[k] - src[k] for k in range(3)]
+        amin = torch.zeros_like(U)
+        amax = torch.ones_like(U)
+        for k in range(3):
+            a0 = (b0[k] - src[k]) / d[k]
+            a1 = (b0[k] + n[k] * w[k] - src[k]) / d[k]
+            amin = torch.maximum(amin, torch.minimum(a0, a1))
+            amax = torch.minimum(amax, torch.maximum(a0, a1))
+        hit = amin < amax
+        eps = 1e-9
+        cnt = torch.ones_like(U)
+        for k in range(3):
+            ce = torch.floor((src[k] + (amin + eps) * d[k] - b0[k]) / w[k])
+            cx_ = torch.floor((src[k] + (amax - eps) * d[k] - b0[k]) / w[k])
+            cnt += torch.abs(cx_ - ce)
+        total += int(torch.where(hit, cnt, torch.zeros_like(cnt)).sum().item())
+    return total
+
+
+# FP32 operations per algorithmic unit (the per-unit figures of the hot-path
+# analysis): projector 10 per non-zero of P (a ray-cell segment), transpose 15
+# per non-zero, sweep per pair evaluation 3*3*(2d+1) for the box-sum patch
+# distance plus 8 for the weight and the two accumulations (one exp besides).
+OPS_PER_NNZ_FORWARD = 10
+OPS_PER_NNZ_BACKPROJECT = 15
+
+
+def sweep_ops_per_pair(d: int) -> int:
+    return 9 * (2 * d + 1) + 8
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) per clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def sweep_pairs(cfg):
     """Pair evaluations of one sweep: every voxel, both directions, every
     window offset that stays inside the volume."""
@@ -248,12 +301,22 @@ def run_ours(args, rank, world, local):
     dom = max(names, key=lambda n: per_launch_ms[n])
     traffic = None
     t = NCU_TRAFFIC.get(dom)
-    if t and t.get("source_sha") == _src_sha(KERNEL_SRC[dom]):
+    if t and t.get("source_sha") == _src_sha(KERNEL_SRC[dom]) and cfg.n_phases == 10:
         traffic = t["bytes_per_launch"]
-    dom_gbs = abytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(dom_gbs, 2), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(dom_gbs / peaks["hbm_gbs"], 5), "traffic": traffic,
-                "peak_source": peaks["_source"] + " (burst copy)"}
+    # the three kernels are bound by FP32 / integer issue, not HBM: roofline against the FP32 peak
+    nnz = projection_nnz(pb.geom)
+    work = {"k_forward": OPS_PER_NNZ_FORWARD * nnz, "k_backproject": OPS_PER_NNZ_BACKPROJECT * nnz,
+            "k_sweep": sweep_ops_per_pair(cfg.d) * sweep_pairs(cfg)}
+    peak_t = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    alu = {n: {"algorithmic_tflop": round(work[n] / 1e12, 4),
+               "achieved_tflops": round(work[n] / (per_launch_ms[n] / 1e3) / 1e12, 3),
+               "frac_of_fp32_peak": round(work[n] / (per_launch_ms[n] / 1e3) / 1e12 / peak_t, 4)} for n in names}
+    roofline = {"bound": "alu", "kernel": dom, "achieved": alu[dom]["achieved_tflops"], "peak": round(peak_t, 2),
+                "unit": "TFLOP/s", "frac": alu[dom]["frac_of_fp32_peak"], "traffic": traffic,
+                "peak_source": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 FLOP x max SM clock "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peaks['_source']} peaks file)",
+                "work": f"{work[dom]:.4g} FP32 ops per launch (nnz(P) = {nnz:.4g})",
+                "hbm_frac": hbm[dom]["frac_of_hbm"]}
     nvox_upd = cfg.n_phases * cfg.vol[0] * cfg.vol[1] * cfg.vol[2]
     sweep_s = per_launch_ms["k_sweep"] / 1e3
     line = {
@@ -270,6 +333,7 @@ def run_ours(args, rank, world, local):
         "tnlm_pair_evals_per_s": round(sweep_pairs(cfg) / sweep_s, 1),
         "stage_ms_per_launch": {n: round(per_launch_ms[n], 4) for n in names},
         "hbm": hbm,
+        "alu": alu,
         "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": int(sum(stage_n)),

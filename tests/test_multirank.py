@@ -46,3 +46,22 @@ def test_two_rank_timing_and_aggregation():
 def test_single_rank_defaults():
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.job_throughput(5, 1, 500.0) == pytest.approx(10.0)
+
+
+def test_projection_nnz_counts_dense_matrix(ora):
+    """The benchmark's algorithmic unit for the projector pair, nnz(P), equals
+    the number of non-zeros of the oracle's dense P on a small geometry."""
+    import numpy as np
+
+    from paper_1201_2450_gb300 import synth
+    g = synth.make_geometry(nx=6, ny=5, nz=4, dx=1.0, nu=12, nv=8, du=1.3, sad=40, sdd=60, n_phases=2,
+                            views_per_phase=3, angle_offset=0.1)
+    G = ora.Geometry(g)
+    cols = []
+    for ph in range(2):
+        for v in range(6 * 5 * 4):
+            e = np.zeros(G.vol_shape)
+            e.reshape(2, -1)[ph, v] = 1.0
+            cols.append(ora.project(G, e).ravel())
+    P = np.stack(cols, 1)
+    assert bench.projection_nnz(g, "cpu") == int((P > 1e-12).sum())
