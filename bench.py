@@ -47,9 +47,9 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # measured on; a changed source invalidates the figure (reported as null).
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload
-    "k_forward": {"bytes_per_launch": int((272.267776e6 + 147.883008e6) * 10 / 6), "source_sha": "0ad0d5313e057fc5"},
-    "k_backproject": {"bytes_per_launch": int((256.100608e6 + 84.198656e6) * 10 / 6), "source_sha": "0ad0d5313e057fc5"},
-    "k_sweep": {"bytes_per_launch": int((161.4336e6 + 83.991808e6) * 10 / 6), "source_sha": "c52872dcd2f275b9"},
+    "k_forward": {"bytes_per_launch": int((270.937344e6 + 148.07168e6) * 10 / 6), "source_sha": "08659ac9224f4ad0"},
+    "k_backproject": {"bytes_per_launch": int((257.549056e6 + 84.06528e6) * 10 / 6), "source_sha": "08659ac9224f4ad0"},
+    "k_sweep": {"bytes_per_launch": int((162.815232e6 + 84.133888e6) * 10 / 6), "source_sha": "804f2d99419ea900"},
 }
 
 
@@ -354,15 +354,15 @@ def run_ours(args, rank, world, local):
 def cpu_baseline_sample(cfg, pb=None) -> dict:
     """Time the FP64 oracle as it stands on a bounded sample of one FBS
     iteration of the workload and extrapolate to iterations/s:
-    projection and transpose of 2 views (x 360 views), one sweep on a
-    3-phase 256 x 256 x 4 slab (x voxel-updates of 10 x 256^2 x 64)."""
+    projection and transpose of 8 views (x 360 views), one sweep on a
+    3-phase 256 x 256 x 8 slab (x voxel-updates of 10 x 256^2 x 64)."""
     import oracle
     from paper_1201_2450_gb300 import synth
 
     oracle.build()
     geom = cfg.geometry() if pb is None else pb.geom
     truth = (pb.truth.cpu() if pb is not None else synth.rasterize(geom, synth._objects(cfg))).numpy()
-    nview = 2
+    nview = 8
     sub = dict(geom)
     sub["nviews"] = np.array([nview], np.int32)
     sub["angles"] = np.asarray(geom["angles"][:nview])
@@ -373,15 +373,15 @@ def cpu_baseline_sample(cfg, pb=None) -> dict:
     t1 = time.perf_counter()
     oracle.backproject(G1, p)
     t2 = time.perf_counter()
-    slab = truth[:3, 30:34].astype(np.float64)
+    slab = truth[:3, 28:36].astype(np.float64)
     oracle.gj_sweep(slab, slab, slab, cfg.d, cfg.M, cfg.h, cfg.mu, 1)
     t3 = time.perf_counter()
     n_views = int(np.sum(geom["nviews"]))
     per_iter = (t1 - t0) / nview * n_views + (t2 - t1) / nview * n_views + \
-        (t3 - t2) * (cfg.n_phases * cfg.vol[2]) / (3 * 4)
+        (t3 - t2) * (cfg.n_phases * cfg.vol[2]) / (3 * 8)
     return {"value": round(1.0 / per_iter, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle: P and P^T of {nview} views (x{n_views}), one sweep on 3 phases x 256x256x4 "
-                      f"(x{cfg.n_phases * cfg.vol[2] / 12:.1f}); {t3 - t0:.1f} s measured, "
+            "sample": f"FP64 oracle: P and P^T of {nview} views (x{n_views}), one sweep on 3 phases x 256x256x8 "
+                      f"(x{cfg.n_phases * cfg.vol[2] / 24:.1f}); {t3 - t0:.1f} s measured, "
                       f"{per_iter:.1f} s per iteration extrapolated"}
 
 
