@@ -67,6 +67,22 @@ static tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n
     return TNLM_OK;
 }
 
+// Column prefix sums for the band transpose: allocated on first use when the
+// geometry admits that transpose; if the allocation fails the exact per-cell
+// transpose runs instead (same results, slower).
+static float *prefix_workspace(tnlm_geometry *g)
+{
+    if (!bands_apply(g->kg)) return nullptr;
+    if (!g->d_pref) {
+        if (cudaMalloc(reinterpret_cast<void **>(&g->d_pref), sizeof(float) * prefix_floats(g->kg, g->n_views_total)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            g->d_pref = nullptr;
+        }
+    }
+    return g->d_pref;
+}
+
 // Records CUDA events around the launches of one stage when timing is on.
 struct StageTimer {
     tnlm_geometry *g;
@@ -232,6 +248,7 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_tmp);
     cudaFree(g->d_part);
     cudaFree(g->d_scalars);
+    cudaFree(g->d_pref);
     delete g;
 }
 
@@ -246,8 +263,9 @@ tnlm_status tnlm_backproject(const tnlm_geometry *g, const float *proj, float *v
 {
     if (!g || !vol || !proj) return arg_error("geometry, proj and vol must not be NULL");
     if (!std::isfinite(alpha) || !std::isfinite(beta)) return arg_error("alpha and beta must be finite");
+    tnlm_geometry *gm = const_cast<tnlm_geometry *>(g);  // the handle's workspace is mutable state
     return launch_backproject(g->kg, g->d_views, g->d_view_off, proj, vol, vol, alpha, beta, false,
-                              as_stream(stream));
+                              prefix_workspace(gm), g->n_views_total, as_stream(stream));
 }
 
 tnlm_status tnlm_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w_out,
@@ -309,7 +327,7 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
             if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
             timer.begin(1);
             TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, geo->d_g, -p->tau, 1.0f,
-                                        true, st));
+                                        true, prefix_workspace(geo), geo->n_views_total, st));
             timer.end();
         }
         // steps 2-4: weights from g^(k) fused into one Eq. 8 sweep, positivity
@@ -377,7 +395,8 @@ tnlm_status tnlm_operator_norm(tnlm_geometry *geo, float *x, int n_iter, double 
         TNLM_TRY(launch_normalize(x, nv, geo->d_scalars, st));
         TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, x, nullptr, geo->d_r, nullptr, 0, st));
         TNLM_TRY(launch_sumsq(geo->d_r, npr, geo->d_part, (int)geo->part_len, geo->d_scalars + 1, st));
-        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, x, x, 1.0f, 0.0f, false, st));
+        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, x, x, 1.0f, 0.0f, false,
+                                    prefix_workspace(geo), geo->n_views_total, st));
     }
     TNLM_TRY_CUDA(cudaMemcpyAsync(L_out, geo->d_scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     TNLM_TRY_CUDA(cudaStreamSynchronize(st));

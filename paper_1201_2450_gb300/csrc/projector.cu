@@ -328,6 +328,160 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
     }
 }
 
+// Exclusive prefix sums along each detector column (fixed view and iu) of the
+// ray-length-scaled projection, accumulated in FP64 and stored as an
+// (hi, lo) float pair: pref[vg][iv][iu] = sum_{t < iv} r(t) |D(t)|.  A sum over
+// a run of rows is then two loads and a difference, exact to FP32 rounding.
+template <bool SCALED>
+__global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restrict__ proj, float2 *__restrict__ pref)
+{
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int vg = blockIdx.y;
+    if (iu >= G.nu) return;
+    const float u = ((float)iu - G.uc) * G.du + G.u_off;
+    const float len_u2 = G.sdd * G.sdd + u * u;
+    const float *__restrict__ pc = proj + (long long)vg * G.npix + iu;
+    float2 *__restrict__ po = pref + (long long)vg * (G.nv + 1) * G.nu + iu;
+    double acc = 0.0;
+    po[0] = make_float2(0.f, 0.f);
+    for (int iv = 0; iv < G.nv; ++iv) {
+        float r = __ldg(pc + (long long)iv * G.nu);
+        if (!SCALED) {
+            const float v = ((float)iv - G.vc) * G.dv + G.v_off;
+            r *= sqrtf(len_u2 + v * v);
+        }
+        acc += (double)r;
+        const float hi = (float)acc;
+        po[(long long)(iv + 1) * G.nu] = make_float2(hi, (float)(acc - (double)hi));
+    }
+}
+
+// Transpose for geometries where a ray's chord through one voxel column spans
+// at most two z cells.  For each view and pixel column iu, the rows of the
+// column chunk split into (i) band rows, whose chord crosses a z boundary
+// z_m: one exact crossing parameter splits the xy chord dg between cells m-1
+// and m; (ii) full rows between two bands, whose chord stays inside one cell:
+// they add r |D| dg each, summed with two prefix-sum loads.  Equal to the
+// per-cell exact tests of k_backproject up to rounding.
+template <bool SCALED>
+__global__ void __launch_bounds__(kBpBX *kBpBY)
+    k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
+                        const float *__restrict__ proj, const float2 *__restrict__ pref, const float *vin,
+                        float *vout, float alpha, float beta, int nchunks)
+{
+    constexpr int NT = kBpBX * kBpBY;
+    extern __shared__ float4 sm4[];
+    float4 *s_row = sm4;  // per detector row: (v, 1/v or 0, v^2, 0)
+    const int tid = threadIdx.y * kBpBX + threadIdx.x;
+    for (int t = tid; t < G.nv; t += NT) {
+        const float v = ((float)t - G.vc) * G.dv + G.v_off;
+        s_row[t] = make_float4(v, v != 0.f ? 1.0f / v : 0.f, v * v, 0.f);
+    }
+    __syncthreads();
+    const int ix = blockIdx.x * kBpBX + threadIdx.x;
+    const int iy = blockIdx.y * kBpBY + threadIdx.y;
+    const int phase = blockIdx.z / nchunks;
+    const int iz0 = (blockIdx.z % nchunks) * kBpCH;
+    if (ix >= G.nx || iy >= G.ny) return;
+    const int nzc = min(kBpCH, G.nz - iz0);
+    const float xc = G.b0x + ((float)ix + 0.5f) * G.dx;
+    const float yc = G.b0y + ((float)iy + 0.5f) * G.dy;
+    const float fvscale = G.inv_dv, fvoff = G.vc - G.v_off * G.inv_dv;  // row coordinate of v: v*fvscale + fvoff
+    float zbd[kBpCH + 1];                                               // z of the chunk's cell boundaries
+#pragma unroll
+    for (int m = 0; m <= kBpCH; ++m) zbd[m] = fmaf((float)(iz0 + m), G.dz, G.b0z);
+    float acc[kBpCH];
+#pragma unroll
+    for (int k = 0; k < kBpCH; ++k) acc[k] = 0.f;
+
+    const int v_end = view_off[phase + 1];
+    for (int vg = view_off[phase]; vg < v_end; ++vg) {
+        const float c = views[vg].c, s = views[vg].s;
+        const float a = xc * c + yc * s;   // view-frame coordinate toward the source
+        const float b = -xc * s + yc * c;  // view-frame coordinate along u
+        const float ac = (G.sad - a) * G.inv_sdd;  // ray parameter at the column centre's depth
+        float umin = FLT_MAX, umax = -FLT_MAX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float ex = (q & 1) ? G.hx : -G.hx, ey = (q & 2) ? G.hy : -G.hy;
+            const float ak = a + ex * c + ey * s;
+            const float bk = b - ex * s + ey * c;
+            const float uk = bk * G.sdd / (G.sad - ak);
+            umin = fminf(umin, uk);
+            umax = fmaxf(umax, uk);
+        }
+        const float fu_lo = fmaxf((umin - G.u_off) * G.inv_du + G.uc - 1e-3f, -1.f);
+        const float fu_hi = fminf((umax - G.u_off) * G.inv_du + G.uc + 1e-3f, (float)G.nu);
+        const int iu_lo = max(0, (int)ceilf(fu_lo));
+        const int iu_hi = min(G.nu - 1, (int)floorf(fu_hi));
+        const float *__restrict__ pv = proj + (long long)vg * G.npix;
+        const float2 *__restrict__ ppv = pref + (long long)vg * (G.nv + 1) * G.nu;
+        for (int iu = iu_lo; iu <= iu_hi; ++iu) {
+            const float u = ((float)iu - G.uc) * G.du + G.u_off;
+            const float w = ac * u - b;
+            const float qx = -w * s, qy = w * c;
+            const float gx = -G.sdd * c - u * s;
+            const float gy = -G.sdd * s + u * c;
+            float glo = -ac, ghi = 1.f - ac;
+            bool ok = true;
+            slab_local(qx, gx, G.hx, glo, ghi, ok);
+            slab_local(qy, gy, G.hy, glo, ghi, ok);
+            if (!ok || !(glo < ghi)) continue;
+            const float dg = ghi - glo;  // xy chord of this pixel column (ray-parameter units)
+            const float sra = fvscale / (ac + glo), srb = fvscale / (ac + ghi);
+            const float len_u2 = G.sdd * G.sdd + u * u;
+            const float *__restrict__ pc = pv + iu;
+            const float2 *__restrict__ pp = ppv + iu;
+            // row images of every boundary at the near and far end of the xy chord
+            int blo[kBpCH + 1], bhi[kBpCH + 1];
+#pragma unroll
+            for (int m = 0; m <= kBpCH; ++m) {
+                const float pa = fmaf(zbd[m], sra, fvoff), pb = fmaf(zbd[m], srb, fvoff);
+                blo[m] = __float2int_ru(fmaxf(fminf(pa, pb) - 1e-3f, -1.f));
+                bhi[m] = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
+            }
+#pragma unroll
+            for (int m = 0; m <= kBpCH; ++m) {
+                if (m > nzc) break;
+                // band rows of boundary m: split the chord at the crossing of z = zbd[m]
+                const int r0 = max(0, blo[m]), r1 = min(G.nv - 1, bhi[m]);
+                for (int iv = r0; iv <= r1; ++iv) {
+                    const float4 rw = s_row[iv];
+                    float r = __ldg(pc + iv * G.nu);
+                    if (!SCALED) r *= sqrtf(len_u2 + rw.z);
+                    float below;  // part of the chord below z = zbd[m]
+                    if (rw.x != 0.f) {
+                        const float gs = fmaf(-ac, rw.x, zbd[m]) * rw.y;  // crossing parameter (column-relative)
+                        below = rw.x > 0.f ? fminf(fmaxf(gs - glo, 0.f), dg) : fminf(fmaxf(ghi - gs, 0.f), dg);
+                    } else {
+                        below = zbd[m] > 0.f ? dg : 0.f;  // ray in the plane z = 0 (half-open cells)
+                    }
+                    if (m > 0) acc[m - 1] = fmaf(r, below, acc[m - 1]);
+                    if (m < nzc) acc[m] = fmaf(r, dg - below, acc[m]);
+                }
+                // full rows of cell m: strictly between the bands of boundaries m and m+1
+                if (m < nzc) {
+                    const int f0 = max(0, bhi[m] + 1), f1 = min(G.nv - 1, blo[m + 1] - 1);
+                    if (f0 <= f1) {
+                        const float2 e0 = __ldg(pp + (long long)f0 * G.nu);
+                        const float2 e1 = __ldg(pp + (long long)(f1 + 1) * G.nu);
+                        acc[m] = fmaf((e1.x - e0.x) + (e1.y - e0.y), dg, acc[m]);
+                    }
+                }
+            }
+        }
+    }
+    const long long base = (long long)phase * G.nvox + ((long long)iz0 * G.ny + iy) * G.nx + ix;
+#pragma unroll
+    for (int k = 0; k < kBpCH; ++k) {
+        if (k < nzc) {
+            const long long o = base + (long long)k * G.nx * G.ny;
+            const float bp = alpha * acc[k];
+            vout[o] = beta != 0.f ? fmaf(beta, vin[o], bp) : bp;
+        }
+    }
+}
+
 }  // namespace
 
 long long forward_blocks(const KGeom &kg, int n_views_total)
@@ -348,13 +502,47 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
     return TNLM_OK;
 }
 
+bool bands_apply(const KGeom &kg)
+{
+    // a ray's chord through one voxel column rises by at most |v|max / SDD per mm of horizontal path,
+    // over at most the column's xy diagonal: keep it well below one cell height
+    const double vmax = 0.5 * (kg.nv - 1) * (double)kg.dv + fabs((double)kg.v_off);
+    const double rise = sqrt((double)kg.dx * kg.dx + (double)kg.dy * kg.dy) * vmax / (double)kg.sdd;
+    return rise <= 0.9 * (double)kg.dz;
+}
+
+size_t prefix_floats(const KGeom &kg, int n_views_total)
+{
+    return (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu;
+}
+
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
-                               const float *vin, float *vout, float alpha, float beta, bool scaled,
-                               cudaStream_t st)
+                               const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
+                               int n_views_total, cudaStream_t st)
 {
     const int nchunks = (kg.nz + kBpCH - 1) / kBpCH;
     dim3 block(kBpBX, kBpBY);
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchunks);
+    if (pref_ws && bands_apply(kg)) {
+        float2 *pref = reinterpret_cast<float2 *>(pref_ws);
+        dim3 sg((kg.nu + 255) / 256, n_views_total);
+        if (scaled)
+            k_colscan<true><<<sg, 256, 0, st>>>(kg, proj, pref);
+        else
+            k_colscan<false><<<sg, 256, 0, st>>>(kg, proj, pref);
+        TNLM_TRY_CUDA(cudaGetLastError());
+        const size_t smem = sizeof(float4) * kg.nv;
+        if (smem > 48 * 1024) {
+            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        if (scaled)
+            k_backproject_bands<true><<<grid, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchunks);
+        else
+            k_backproject_bands<false><<<grid, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchunks);
+        TNLM_TRY_CUDA(cudaGetLastError());
+        return TNLM_OK;
+    }
     const size_t smem = sizeof(float4) * kg.nv + sizeof(float) * kBpCH * kBpBX * kBpBY;
     if (smem > 48 * 1024) {
         TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -60,9 +60,13 @@ long long forward_blocks(const KGeom &kg, int n_views_total);
 
 // vout = beta * vin + alpha * P^T proj.  scaled: proj already multiplied by
 // the ray length |source -> pixel| (the residual form written by mode 1).
+// pref_ws (nullable): prefix_floats() floats of workspace; when given and the
+// geometry allows it (bands_apply), the band/prefix-sum transpose runs.
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
-                               const float *vin, float *vout, float alpha, float beta, bool scaled,
-                               cudaStream_t st);
+                               const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
+                               int n_views_total, cudaStream_t st);
+bool bands_apply(const KGeom &kg);
+size_t prefix_floats(const KGeom &kg, int n_views_total);
 
 tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
                          float *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
@@ -99,6 +103,7 @@ struct tnlm_geometry {
     double *d_part = nullptr;         // forward-projector partial sums
     long long part_len = 0;
     double *d_scalars = nullptr;      // reduction results
+    float *d_pref = nullptr;          // column prefix sums for the transpose (prefix_floats)
     long long scalars_len = 0;
     // instrumentation
     int timing = 0;

@@ -94,6 +94,24 @@ def test_project_odd_detector_face_rays(ora):
     assert rel_l2(tnlm.tnlm_project(G, cuda(x)).cpu().numpy(), ora.project(ora.Geometry(geom), x)) <= RTOL
 
 
+def test_backproject_thin_slices_fallback(ora):
+    """Thin slices and a tall detector: a chord can span several z cells, so the
+    library takes its exact per-cell transpose instead of the band/prefix-sum
+    one; both must match the oracle."""
+    geom = synth.make_geometry(nx=12, ny=10, nz=20, dx=1.0, dz=0.15, nu=40, nv=64, du=1.0, dv=2.0, sad=150.0,
+                               sdd=300.0, n_phases=2, views_per_phase=[3, 4], angle_offset=0.2)
+    G = tnlm.Geometry(geom)
+    y = synth.uniform(G.proj_shape, 108)
+    out = tnlm.tnlm_backproject(G, cuda(y)).cpu().numpy()
+    assert rel_l2(out, ora.backproject(ora.Geometry(geom), y)) <= RTOL
+    x = cuda(synth.uniform(G.vol_shape, 109))
+    px = tnlm.tnlm_project(G, x)
+    bty = tnlm.tnlm_backproject(G, cuda(y))
+    lhs = float((px.double() * cuda(y).double()).sum())
+    rhs = float((x.double() * bty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * float(px.double().norm() * cuda(y).double().norm())
+
+
 WEIGHT_CASES = [((3, 7, 10, 12), 1, 2, 0.5), ((2, 5, 6, 9), 2, 1, 0.8), ((4, 4, 4, 4), 0, 2, 0.3),
                 ((2, 6, 5, 7), 1, 3, 0.5)]
 
