@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
 // they add r |D| dg each, summed with two prefix-sum loads.  Equal to the
 // per-cell exact tests of k_backproject up to rounding.
 template <bool SCALED>
-__global__ void __launch_bounds__(kBpBX *kBpBY)
+__global__ void __launch_bounds__(kBpBX *kBpBY, 10)
     k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
                         const float *__restrict__ proj, const float2 *__restrict__ pref, const float *vin,
                         float *vout, float alpha, float beta, int nchunks)
@@ -402,9 +402,6 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
     const float xc = G.b0x + ((float)ix + 0.5f) * G.dx;
     const float yc = G.b0y + ((float)iy + 0.5f) * G.dy;
     const float fvscale = G.inv_dv, fvoff = G.vc - G.v_off * G.inv_dv;  // row coordinate of v: v*fvscale + fvoff
-    float zbd[kBpCH + 1];                                               // z of the chunk's cell boundaries
-#pragma unroll
-    for (int m = 0; m <= kBpCH; ++m) zbd[m] = fmaf((float)(iz0 + m), G.dz, G.b0z);
     float acc[kBpCH];
 #pragma unroll
     for (int k = 0; k < kBpCH; ++k) acc[k] = 0.f;
@@ -447,42 +444,53 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
             const float len_u2 = G.sdd * G.sdd + u * u;
             const float *__restrict__ pc = pv + iu;
             const float2 *__restrict__ pp = ppv + iu;
-            // row images of every boundary at the near and far end of the xy chord
-            int blo[kBpCH + 1], bhi[kBpCH + 1];
-#pragma unroll
-            for (int m = 0; m <= kBpCH; ++m) {
-                const float pa = fmaf(zbd[m], sra, fvoff), pb = fmaf(zbd[m], srb, fvoff);
-                blo[m] = __float2int_ru(fmaxf(fminf(pa, pb) - 1e-3f, -1.f));
-                bhi[m] = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
+            // row images of boundary m at the near and far end of the xy chord; boundary m+1 is mapped
+            // one step ahead because the full rows of cell m end where its band begins
+            float zm = fmaf((float)iz0, G.dz, G.b0z);
+            int blo_m, bhi_m;
+            {
+                const float pa = fmaf(zm, sra, fvoff), pb = fmaf(zm, srb, fvoff);
+                blo_m = __float2int_ru(fmaxf(fminf(pa, pb) - 1e-3f, -1.f));
+                bhi_m = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
             }
 #pragma unroll
             for (int m = 0; m <= kBpCH; ++m) {
                 if (m > nzc) break;
-                // band rows of boundary m: split the chord at the crossing of z = zbd[m]
-                const int r0 = max(0, blo[m]), r1 = min(G.nv - 1, bhi[m]);
+                const float zn = fmaf((float)(iz0 + m + 1), G.dz, G.b0z);
+                int blo_n, bhi_n;
+                {
+                    const float pa = fmaf(zn, sra, fvoff), pb = fmaf(zn, srb, fvoff);
+                    blo_n = __float2int_ru(fmaxf(fminf(pa, pb) - 1e-3f, -1.f));
+                    bhi_n = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
+                }
+                // band rows of boundary m: split the chord at the crossing of z = zm
+                const int r0 = max(0, blo_m), r1 = min(G.nv - 1, bhi_m);
                 for (int iv = r0; iv <= r1; ++iv) {
                     const float4 rw = s_row[iv];
                     float r = __ldg(pc + iv * G.nu);
                     if (!SCALED) r *= sqrtf(len_u2 + rw.z);
-                    float below;  // part of the chord below z = zbd[m]
+                    float below;  // part of the chord below z = zm
                     if (rw.x != 0.f) {
-                        const float gs = fmaf(-ac, rw.x, zbd[m]) * rw.y;  // crossing parameter (column-relative)
+                        const float gs = fmaf(-ac, rw.x, zm) * rw.y;  // crossing parameter (column-relative)
                         below = rw.x > 0.f ? fminf(fmaxf(gs - glo, 0.f), dg) : fminf(fmaxf(ghi - gs, 0.f), dg);
                     } else {
-                        below = zbd[m] > 0.f ? dg : 0.f;  // ray in the plane z = 0 (half-open cells)
+                        below = zm > 0.f ? dg : 0.f;  // ray in the plane z = 0 (half-open cells)
                     }
                     if (m > 0) acc[m - 1] = fmaf(r, below, acc[m - 1]);
                     if (m < nzc) acc[m] = fmaf(r, dg - below, acc[m]);
                 }
                 // full rows of cell m: strictly between the bands of boundaries m and m+1
                 if (m < nzc) {
-                    const int f0 = max(0, bhi[m] + 1), f1 = min(G.nv - 1, blo[m + 1] - 1);
+                    const int f0 = max(0, bhi_m + 1), f1 = min(G.nv - 1, blo_n - 1);
                     if (f0 <= f1) {
                         const float2 e0 = __ldg(pp + (long long)f0 * G.nu);
                         const float2 e1 = __ldg(pp + (long long)(f1 + 1) * G.nu);
                         acc[m] = fmaf((e1.x - e0.x) + (e1.y - e0.y), dg, acc[m]);
                     }
                 }
+                zm = zn;
+                blo_m = blo_n;
+                bhi_m = bhi_n;
             }
         }
     }
