@@ -81,6 +81,10 @@ typedef struct {
     int n_inner;      /* TNLM-R: gradient steps per (P1) (>= 1) */
     int clip_nonneg;  /* 1: positivity correction f <- max(f, 0) after Eq. 8 (TNLM-R step 4) */
     int gj_start;     /* TNLM-R: 0 = Eq. 8 iterate starts at g^(k) (default), 1 = at f^(k-1) */
+    int n_gj;         /* TNLM-R: Eq. 8 iterations per (P2), weights of g^(k) frozen; the paper uses 1
+                         (Sec. 2.3); 0 is read as 1.  Positivity follows the last iteration. */
+    int p1_solver;    /* TNLM-R: 0 = n_inner gradient steps with step tau; 1 = n_inner CGLS iterations
+                         (the paper's solver, Sec. 2.3), tau unused */
 } tnlm_params;
 
 /* Create a geometry handle from `desc` (copied; the desc arrays may be freed
@@ -128,11 +132,13 @@ tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float 
                               void *stream);
 
 /* TNLM-R (Sec. 2.3): f holds f^(0) on entry and f^(n_outer) on exit.  Each
- * FBS iteration k: (P1) n_inner gradient steps g <- g - tau P^T (P g - y)
- * from g = f^(k-1); weights from g^(k) (Eq. 9); one Eq. 8 sweep; positivity
- * when clip_nonneg.  y: [sum n_views][nv][nu].  report (HOST pointer,
- * nullable) receives ||P g - y||^2 (FP64) before every gradient step,
- * [n_outer][n_inner]; when it is given the call synchronises `stream`.
+ * FBS iteration k: (P1) from g = f^(k-1) by n_inner gradient steps
+ * g <- g - tau P^T (P g - y), or n_inner CGLS iterations (p1_solver = 1);
+ * weights from g^(k) (Eq. 9); n_gj Eq. 8 sweeps (one in
+ * the paper); positivity when clip_nonneg.  y: [sum n_views][nv][nu].  report (HOST pointer,
+ * nullable) receives ||P g - y||^2 (FP64) before every gradient step or CGLS
+ * iteration, [n_outer][n_inner]; when it is given the call synchronises
+ * `stream`.
  * The first call allocates the handle's workspace (cudaMalloc, about
  * sum(n_views) nu nv + N_p nx ny nz floats); make it before any capture. */
 tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, const tnlm_params *params,
@@ -166,6 +172,16 @@ tnlm_status tnlm_enhance(int nx, int ny, int nz, int n_phases, const float *g, f
  * Arguments are those of tnlm_enhance. */
 tnlm_status tnlm_enhance_noalloc(int nx, int ny, int nz, int n_phases, const float *g, float *f,
                                  const tnlm_params *params, void *stream);
+
+/* (P1) of Eq. 5 by CGLS (conjugate gradients for least squares, the
+ * paper's ref. 37, Sec. 2.3): n_iter iterations on min ||P_i x_i - y_i||^2
+ * from the initial x, phase by phase (the phases are uncoupled in (P1), so
+ * each has its own step and direction scalars).  x: [N_p][nz][ny][nx] in/out;
+ * y: [sum n_views][nv][nu].  report (HOST, nullable) receives
+ * sum_i ||y_i - P_i x_i||^2 before each iteration and after the last,
+ * [n_iter + 1], and makes the call synchronise `stream`.  The first call
+ * allocates CGLS workspace in the handle (two volumes, one projection set). */
+tnlm_status tnlm_cgls(tnlm_geometry *geom, const float *y, float *x, int n_iter, double *report, void *stream);
 
 /* Estimate L = ||P||_2^2 (so tau = 1/L for the (P1) step) by n_iter power
  * iterations on P^T P from the start image x ([N_p][nz][ny][nx], device,

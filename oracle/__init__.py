@@ -79,7 +79,8 @@ def _load():
             "ora_gj_sweep": (None, [i, i, i, i, _dp, _dp, _dp, i, i, d, d, i, _dp]),
             "ora_tnlm_energy": (d, [i, i, i, i, _dp, i, _dp]),
             "ora_fidelity": (d, [G, _dp, _dp]),
-            "ora_reconstruct": (None, [G, _dp, _dp, d, i, i, d, d, i, i, i, i, C.c_void_p]),
+            "ora_reconstruct": (None, [G, _dp, _dp, d, i, i, d, d, i, i, i, i, i, i, C.c_void_p]),
+            "ora_cgls": (None, [G, _dp, _dp, i, C.c_void_p]),
             "ora_enhance": (None, [i, i, i, i, _dp, _dp, i, i, d, d, i, i]),
             "ora_num_threads": (i, []),
         }
@@ -213,13 +214,24 @@ def fidelity(geom: Geometry, f, y) -> float:
 
 
 def reconstruct(geom: Geometry, y, f0, tau: float, d: int, M: int, h: float, mu: float, n_outer: int,
-                n_inner: int = 1, clip: int = 1, gj_start: int = 0, with_report: bool = False):
-    """TNLM-R (Sec. 2.3) with (P1) solved by n_inner gradient steps."""
+                n_inner: int = 1, clip: int = 1, gj_start: int = 0, with_report: bool = False, n_gj: int = 1,
+                p1_cgls: int = 0):
+    """TNLM-R (Sec. 2.3) with (P1) solved by n_inner gradient steps and (P2)
+    by n_gj Eq. 8 iterations."""
     f = _f64(f0).reshape(geom.vol_shape).copy()
     rep = np.zeros((n_outer, n_inner), np.float64) if with_report else None
     _load().ora_reconstruct(geom.ref, _f64(y).reshape(geom.proj_shape), f, tau, d, M, h, mu, n_outer, n_inner,
-                            clip, gj_start, rep.ctypes.data if rep is not None else None)
+                            n_gj, clip, gj_start, p1_cgls, rep.ctypes.data if rep is not None else None)
     return (f, rep) if with_report else f
+
+
+def cgls(geom: Geometry, y, x0, n_iter: int, with_report: bool = False):
+    """(P1) by CGLS phase by phase from x0; returns x (and the residual norms)."""
+    x = _f64(x0).reshape(geom.vol_shape).copy()
+    rep = np.zeros(n_iter + 1) if with_report else None
+    _load().ora_cgls(geom.ref, _f64(y).reshape(geom.proj_shape), x, n_iter,
+                     rep.ctypes.data if rep is not None else None)
+    return (x, rep) if with_report else x
 
 
 def enhance(g, d: int, M: int, h: float, mu: float, n_sweeps: int, clip: int = 0) -> np.ndarray:

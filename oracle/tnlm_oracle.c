@@ -542,10 +542,77 @@ double ora_fidelity(const ora_geom *g, const double *f, const double *yproj)
 /* TNLM-R and TNLM-E (Sec. 2.3 algorithm boxes)                         */
 /* ------------------------------------------------------------------ */
 
+/* (P1) of Eq. 5 by CGLS (conjugate gradients for least squares, the paper's
+ * ref. 37, named in Sec. 2.3), run phase by phase because the phases are
+ * uncoupled in (P1): every phase has its own step and direction scalars.
+ * x holds the initial value on entry and the iterate after n_iter steps on
+ * exit.  report (nullable) receives sum_i ||y_i - P_i x_i||^2 before every
+ * step and after the last, [n_iter + 1]. */
+void ora_cgls(const ora_geom *g, const double *yproj, double *x, int n_iter, double *report)
+{
+    const int np_ = g->np;
+    const long nvox = ora_nvox(g), nv = nvox * np_;
+    const long npix = ora_npix(g);
+    const long npr = (long)ora_total_views(g) * npix;
+    double *r = (double *)malloc(sizeof(double) * npr);
+    double *q = (double *)malloc(sizeof(double) * npr);
+    double *s = (double *)malloc(sizeof(double) * nv);
+    double *p = (double *)malloc(sizeof(double) * nv);
+    double *gam = (double *)malloc(sizeof(double) * np_);
+    long *pofs = (long *)malloc(sizeof(long) * (np_ + 1)); /* projection offset of each phase */
+    pofs[0] = 0;
+    for (int i = 0; i < np_; ++i) pofs[i + 1] = pofs[i] + (long)g->nviews[i] * npix;
+
+    ora_project(g, x, r);
+    for (long t = 0; t < npr; ++t) r[t] = yproj[t] - r[t];
+    ora_backproject(g, r, s);
+    memcpy(p, s, sizeof(double) * nv);
+    for (int i = 0; i < np_; ++i) {
+        gam[i] = 0.0;
+        for (long t = 0; t < nvox; ++t) gam[i] += s[i * nvox + t] * s[i * nvox + t];
+    }
+    for (int it = 0; it <= n_iter; ++it) {
+        if (report) {
+            double rr = 0.0;
+            for (long t = 0; t < npr; ++t) rr += r[t] * r[t];
+            report[it] = rr;
+        }
+        if (it == n_iter) break;
+        ora_project(g, p, q);
+        for (int i = 0; i < np_; ++i) {
+            double qq = 0.0;
+            for (long t = pofs[i]; t < pofs[i + 1]; ++t) qq += q[t] * q[t];
+            const double alpha = qq > 0.0 ? gam[i] / qq : 0.0;
+            for (long t = 0; t < nvox; ++t) x[i * nvox + t] += alpha * p[i * nvox + t];
+            for (long t = pofs[i]; t < pofs[i + 1]; ++t) r[t] -= alpha * q[t];
+        }
+        ora_backproject(g, r, s);
+        for (int i = 0; i < np_; ++i) {
+            double gn = 0.0;
+            for (long t = 0; t < nvox; ++t) gn += s[i * nvox + t] * s[i * nvox + t];
+            const double beta = gam[i] > 0.0 ? gn / gam[i] : 0.0;
+            for (long t = 0; t < nvox; ++t) p[i * nvox + t] = s[i * nvox + t] + beta * p[i * nvox + t];
+            gam[i] = gn;
+        }
+    }
+    free(r);
+    free(q);
+    free(s);
+    free(p);
+    free(gam);
+    free(pofs);
+}
+
 /* TNLM-R: f holds f^(0) on entry and the result on exit.  report (nullable)
- * receives ||P g - y||^2 before each gradient step, [n_outer][n_inner]. */
+ * receives ||P g - y||^2 before each gradient step, [n_outer][n_inner].
+ * (P2) runs n_gj Eq. 8 iterations (the paper uses one, Sec. 2.3) with the
+ * weights of g^(k) frozen; the positivity correction follows the last.
+ * p1_cgls selects (P1) = n_inner CGLS iterations (the paper's solver)
+ * instead of n_inner gradient steps with step tau; report then holds the
+ * CGLS residuals before each iteration. */
 void ora_reconstruct(const ora_geom *g, const double *yproj, double *f, double tau, int d, int M, double h,
-                     double mu, int n_outer, int n_inner, int clip, int gj_start, double *report)
+                     double mu, int n_outer, int n_inner, int n_gj, int clip, int gj_start, int p1_cgls,
+                     double *report)
 {
     const long nv = ora_nvox(g) * g->np;
     const long npr = (long)ora_total_views(g) * ora_npix(g);
@@ -553,10 +620,18 @@ void ora_reconstruct(const ora_geom *g, const double *yproj, double *f, double t
     double *bp = (double *)malloc(sizeof(double) * nv);
     double *r = (double *)malloc(sizeof(double) * npr);
     double *fn = (double *)malloc(sizeof(double) * nv);
+    double *fl = (double *)malloc(sizeof(double) * nv);
     for (int k = 0; k < n_outer; ++k) {
         /* step 1: (P1) from the initial value f^(k-1) */
         memcpy(gk, f, sizeof(double) * nv);
-        for (int t = 0; t < n_inner; ++t) {
+        if (p1_cgls) {
+            double *rep = report ? (double *)malloc(sizeof(double) * (n_inner + 1)) : NULL;
+            ora_cgls(g, yproj, gk, n_inner, rep);
+            if (report)
+                for (int t = 0; t < n_inner; ++t) report[(long)k * n_inner + t] = rep[t];
+            free(rep);
+        }
+        for (int t = 0; t < (p1_cgls ? 0 : n_inner); ++t) {
             ora_project(g, gk, r);
             double rn = 0.0;
             for (long q = 0; q < npr; ++q) {
@@ -567,14 +642,19 @@ void ora_reconstruct(const ora_geom *g, const double *yproj, double *f, double t
             ora_backproject(g, r, bp);
             for (long q = 0; q < nv; ++q) gk[q] -= tau * bp[q];
         }
-        /* steps 2-4: weights from g^(k), Eq. 8, positivity */
-        ora_gj_sweep(g->nx, g->ny, g->nz, g->np, gk, gj_start ? f : gk, gk, d, M, h, mu, clip, fn);
-        memcpy(f, fn, sizeof(double) * nv);
+        /* steps 2-4: weights from g^(k), Eq. 8 iterated from f^(l=0), positivity */
+        memcpy(fl, gj_start ? f : gk, sizeof(double) * nv);
+        for (int l = 0; l < n_gj; ++l) {
+            ora_gj_sweep(g->nx, g->ny, g->nz, g->np, gk, fl, gk, d, M, h, mu, clip && l == n_gj - 1, fn);
+            memcpy(fl, fn, sizeof(double) * nv);
+        }
+        memcpy(f, fl, sizeof(double) * nv);
     }
     free(gk);
     free(bp);
     free(r);
     free(fn);
+    free(fl);
 }
 
 /* TNLM-E: f^(0) = g, then n_sweeps times: weights from f^(k), Eq. 8 */

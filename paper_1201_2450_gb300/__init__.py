@@ -27,7 +27,7 @@ from ._build import build
 __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
-    "tnlm_operator_norm",
+    "tnlm_operator_norm", "tnlm_cgls",
     "reconstruct_host", "library_path",
 ]
 
@@ -62,7 +62,8 @@ class _Desc(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("d", C.c_int), ("M", C.c_int), ("h", C.c_float), ("mu", C.c_float), ("tau", C.c_float),
-                ("n_outer", C.c_int), ("n_inner", C.c_int), ("clip_nonneg", C.c_int), ("gj_start", C.c_int)]
+                ("n_outer", C.c_int), ("n_inner", C.c_int), ("clip_nonneg", C.c_int), ("gj_start", C.c_int),
+                ("n_gj", C.c_int), ("p1_solver", C.c_int)]
 
 
 @dataclass
@@ -77,10 +78,12 @@ class Params:
     n_inner: int = 1
     clip_nonneg: int = 1
     gj_start: int = 0
+    n_gj: int = 1
+    p1_solver: int = 0
 
     def _c(self) -> _Params:
         return _Params(self.d, self.M, self.h, self.mu, self.tau, self.n_outer, self.n_inner, self.clip_nonneg,
-                       self.gj_start)
+                       self.gj_start, self.n_gj, self.p1_solver)
 
 
 def library_path() -> str:
@@ -108,6 +111,7 @@ def _load():
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_enhance_noalloc": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
+            "tnlm_cgls": (i, [vp, vp, vp, i, vp, vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
             "tnlm_status_string": (C.c_char_p, [i]),
@@ -283,6 +287,15 @@ def tnlm_enhance_noalloc(g: torch.Tensor, params: Params, out: torch.Tensor, str
     _check(_load().tnlm_enhance_noalloc(nx, ny, nz, np_, _dev(g, "g"), _dev(out, "f", g.device, g.shape),
                                         C.byref(p), _stream(stream)), "tnlm_enhance_noalloc")
     return out
+
+
+def tnlm_cgls(geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, report: bool = False, stream=None):
+    """(P1) by CGLS, phase by phase, in place on x; returns (x, residual norms or None)."""
+    rep = np.zeros(n_iter + 1, np.float64) if report else None
+    _check(_load().tnlm_cgls(geom.handle, _dev(y, "y", geom.device, geom.proj_shape),
+                             _dev(x, "x", geom.device, geom.vol_shape), n_iter,
+                             rep.ctypes.data if rep is not None else None, _stream(stream)), "tnlm_cgls")
+    return x, rep
 
 
 def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:

@@ -67,6 +67,29 @@ static tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n
     return TNLM_OK;
 }
 
+static tnlm_status ensure_cgls_workspace(tnlm_geometry *g)
+{
+    const KGeom &kg = g->kg;
+    TNLM_TRY(dev_alloc(&g->d_q, (size_t)g->n_views_total * kg.npix));
+    TNLM_TRY(dev_alloc(&g->d_s, (size_t)kg.np * kg.nvox));
+    TNLM_TRY(dev_alloc(&g->d_p, (size_t)kg.np * kg.nvox));
+    TNLM_TRY(dev_alloc(&g->d_cscal, (size_t)3 * kg.np));
+    const int npart = cgls_partial_len(kg.np) > sumsq_scratch_len() ? cgls_partial_len(kg.np) : sumsq_scratch_len();
+    TNLM_TRY(dev_alloc(&g->d_cpart, (size_t)npart));
+    if (!g->d_vseg) {
+        std::vector<long long> vs(kg.np + 1), ps(kg.np + 1);
+        for (int i = 0; i <= kg.np; ++i) {
+            vs[i] = (long long)i * kg.nvox;
+            ps[i] = (long long)g->view_off[i] * kg.npix;
+        }
+        TNLM_TRY(dev_alloc(&g->d_vseg, (size_t)kg.np + 1));
+        TNLM_TRY(dev_alloc(&g->d_pseg, (size_t)kg.np + 1));
+        TNLM_TRY_CUDA(cudaMemcpy(g->d_vseg, vs.data(), sizeof(long long) * (kg.np + 1), cudaMemcpyHostToDevice));
+        TNLM_TRY_CUDA(cudaMemcpy(g->d_pseg, ps.data(), sizeof(long long) * (kg.np + 1), cudaMemcpyHostToDevice));
+    }
+    return TNLM_OK;
+}
+
 // Column prefix sums for the band transpose: allocated on first use when the
 // geometry admits that transpose; if the allocation fails the exact per-cell
 // transpose runs instead (same results, slower).
@@ -81,6 +104,29 @@ static float *prefix_workspace(tnlm_geometry *g)
         }
     }
     return g->d_pref;
+}
+
+static CglsArgs cgls_args(tnlm_geometry *g, const float *y, float *x, int n_iter, double *report_dev)
+{
+    CglsArgs a;
+    a.kg = &g->kg;
+    a.views = g->d_views;
+    a.view_off = g->d_view_off;
+    a.n_views_total = g->n_views_total;
+    a.y = y;
+    a.x = x;
+    a.r = g->d_r;
+    a.q = g->d_q;
+    a.s = g->d_s;
+    a.p = g->d_p;
+    a.pref = prefix_workspace(g);
+    a.vseg = g->d_vseg;
+    a.pseg = g->d_pseg;
+    a.scal = g->d_cscal;
+    a.partial = g->d_cpart;
+    a.report_dev = report_dev;
+    a.n_iter = n_iter;
+    return a;
 }
 
 // Records CUDA events around the launches of one stage when timing is on.
@@ -249,6 +295,13 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_part);
     cudaFree(g->d_scalars);
     cudaFree(g->d_pref);
+    cudaFree(g->d_q);
+    cudaFree(g->d_s);
+    cudaFree(g->d_p);
+    cudaFree(g->d_vseg);
+    cudaFree(g->d_pseg);
+    cudaFree(g->d_cscal);
+    cudaFree(g->d_cpart);
     delete g;
 }
 
@@ -301,6 +354,8 @@ static tnlm_status check_params(const tnlm_params *p, bool recon)
         if (p->n_inner < 1) return arg_error("n_inner must be >= 1");
         if (!std::isfinite(p->tau)) return arg_error("tau must be finite");
         if (p->gj_start != 0 && p->gj_start != 1) return arg_error("gj_start must be 0 or 1");
+        if (p->n_gj < 0) return arg_error("n_gj must be >= 0");
+        if (p->p1_solver != 0 && p->p1_solver != 1) return arg_error("p1_solver must be 0 (gradient) or 1 (CGLS)");
     }
     return TNLM_OK;
 }
@@ -313,13 +368,23 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
     const KGeom &kg = geo->kg;
     TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
     const long long n_norms = (long long)p->n_outer * p->n_inner;
-    TNLM_TRY(ensure_workspace(geo, p->gj_start == 1, n_norms > 1 ? n_norms : 1));
+    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
+    TNLM_TRY(ensure_workspace(geo, p->gj_start == 1 || p->n_gj > 1, n_slots > 1 ? n_slots : 1));
+    if (p->p1_solver == 1) TNLM_TRY(ensure_cgls_workspace(geo));
     cudaStream_t st = as_stream(stream);
     StageTimer timer(geo, st);
     const long long nblk = forward_blocks(kg, geo->n_views_total);
     for (int k = 0; k < p->n_outer; ++k) {
-        // step 1: (P1) gradient steps from f^(k-1)
-        for (int t = 0; t < p->n_inner; ++t) {
+        // step 1: (P1) from f^(k-1): CGLS (the paper's solver) or n_inner gradient steps
+        if (p->p1_solver == 1) {
+            timer.begin(0);
+            TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+            TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
+                                        report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
+                              st));
+            timer.end();
+        }
+        for (int t = 0; t < (p->p1_solver == 1 ? 0 : p->n_inner); ++t) {
             const float *src = t == 0 ? f : geo->d_g;
             timer.begin(0);
             TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
@@ -330,21 +395,34 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
                                         true, prefix_workspace(geo), geo->n_views_total, st));
             timer.end();
         }
-        // steps 2-4: weights from g^(k) fused into one Eq. 8 sweep, positivity
+        // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
         timer.begin(2);
-        if (p->gj_start == 0) {
-            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, geo->d_g, geo->d_g, f, p->d, p->M, p->h,
-                                  p->mu, p->clip_nonneg, st));
-        } else {
-            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, f, geo->d_g, geo->d_tmp, p->d, p->M, p->h,
-                                  p->mu, p->clip_nonneg, st));
-            TNLM_TRY_CUDA(cudaMemcpyAsync(f, geo->d_tmp, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+        const int ngj = p->n_gj > 0 ? p->n_gj : 1;
+        const float *vals = p->gj_start ? f : geo->d_g;
+        for (int l = 0; l < ngj; ++l) {
+            // sweeps alternate between f and the scratch image so that the last lands in f; with
+            // gj_start = 1 the first sweep reads f and must write the scratch image
+            float *dst = ((ngj - 1 - l) % 2 == 0) ? f : geo->d_tmp;
+            if (dst == vals) dst = (vals == f) ? geo->d_tmp : f;  // never read and write one image
+            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, vals, geo->d_g, dst, p->d, p->M, p->h,
+                                  p->mu, p->clip_nonneg && l == ngj - 1, st));
+            vals = dst;
         }
+        if (vals != f)
+            TNLM_TRY_CUDA(cudaMemcpyAsync(f, vals, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
         timer.end();
     }
     if (report && n_norms > 0) {
-        TNLM_TRY_CUDA(cudaMemcpyAsync(report, geo->d_scalars, sizeof(double) * n_norms, cudaMemcpyDeviceToHost, st));
-        TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+        if (p->p1_solver == 1) {  // keep the residual before each of the n_inner CGLS iterations
+            std::vector<double> tmp((size_t)n_slots);
+            TNLM_TRY_CUDA(cudaMemcpyAsync(tmp.data(), geo->d_scalars, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, st));
+            TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+            for (int k = 0; k < p->n_outer; ++k)
+                for (int t = 0; t < p->n_inner; ++t) report[(long long)k * p->n_inner + t] = tmp[(size_t)k * (p->n_inner + 1) + t];
+        } else {
+            TNLM_TRY_CUDA(cudaMemcpyAsync(report, geo->d_scalars, sizeof(double) * n_norms, cudaMemcpyDeviceToHost, st));
+            TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+        }
     }
     return timer.finish();
 }
@@ -400,6 +478,21 @@ tnlm_status tnlm_operator_norm(tnlm_geometry *geo, float *x, int n_iter, double 
     }
     TNLM_TRY_CUDA(cudaMemcpyAsync(L_out, geo->d_scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_cgls(tnlm_geometry *geo, const float *y, float *x, int n_iter, double *report, void *stream)
+{
+    if (!geo || !y || !x) return arg_error("geometry, y and x must not be NULL");
+    if (n_iter < 0) return arg_error("n_iter must be >= 0");
+    TNLM_TRY(ensure_workspace(geo, false, (long long)n_iter + 1));
+    TNLM_TRY(ensure_cgls_workspace(geo));
+    cudaStream_t st = as_stream(stream);
+    TNLM_TRY(run_cgls(cgls_args(geo, y, x, n_iter, report ? geo->d_scalars : nullptr), st));
+    if (report) {
+        TNLM_TRY_CUDA(cudaMemcpyAsync(report, geo->d_scalars, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
+        TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+    }
     return TNLM_OK;
 }
 

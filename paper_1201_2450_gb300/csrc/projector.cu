@@ -22,6 +22,7 @@ namespace {
 
 constexpr int kFwdBX = 32, kFwdBY = 4;        // projector block: 32 u x 4 v pixels
 constexpr int kBpBX = 32, kBpBY = 4, kBpCH = 8;  // transpose block: 32 x 4 columns, 8 voxels in z each
+constexpr int kBandCH = 8;                        // z cells per thread in the band transpose
 
 // Enter the slab 0 <= E + b G < n (voxel-index units) into [blo, bhi];
 // a ray parallel to the slab is inside iff 0 <= E < n (half-open cells).
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
 // and m; (ii) full rows between two bands, whose chord stays inside one cell:
 // they add r |D| dg each, summed with two prefix-sum loads.  Equal to the
 // per-cell exact tests of k_backproject up to rounding.
-template <bool SCALED>
+template <bool SCALED, int CH>
 __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
     k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
                         const float *__restrict__ proj, const float2 *__restrict__ pref, const float *vin,
@@ -396,15 +397,15 @@ __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
     const int ix = blockIdx.x * kBpBX + threadIdx.x;
     const int iy = blockIdx.y * kBpBY + threadIdx.y;
     const int phase = blockIdx.z / nchunks;
-    const int iz0 = (blockIdx.z % nchunks) * kBpCH;
+    const int iz0 = (blockIdx.z % nchunks) * CH;
     if (ix >= G.nx || iy >= G.ny) return;
-    const int nzc = min(kBpCH, G.nz - iz0);
+    const int nzc = min(CH, G.nz - iz0);
     const float xc = G.b0x + ((float)ix + 0.5f) * G.dx;
     const float yc = G.b0y + ((float)iy + 0.5f) * G.dy;
     const float fvscale = G.inv_dv, fvoff = G.vc - G.v_off * G.inv_dv;  // row coordinate of v: v*fvscale + fvoff
-    float acc[kBpCH];
+    float acc[CH];
 #pragma unroll
-    for (int k = 0; k < kBpCH; ++k) acc[k] = 0.f;
+    for (int k = 0; k < CH; ++k) acc[k] = 0.f;
 
     const int v_end = view_off[phase + 1];
     for (int vg = view_off[phase]; vg < v_end; ++vg) {
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
                 bhi_m = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
             }
 #pragma unroll
-            for (int m = 0; m <= kBpCH; ++m) {
+            for (int m = 0; m <= CH; ++m) {
                 if (m > nzc) break;
                 const float zn = fmaf((float)(iz0 + m + 1), G.dz, G.b0z);
                 int blo_n, bhi_n;
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
     }
     const long long base = (long long)phase * G.nvox + ((long long)iz0 * G.ny + iy) * G.nx + ix;
 #pragma unroll
-    for (int k = 0; k < kBpCH; ++k) {
+    for (int k = 0; k < CH; ++k) {
         if (k < nzc) {
             const long long o = base + (long long)k * G.nx * G.ny;
             const float bp = alpha * acc[k];
@@ -547,6 +548,9 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
     dim3 block(kBpBX, kBpBY);
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchunks);
     if (pref_ws && bands_apply(kg)) {
+        constexpr int CHB = kBandCH;
+        const int nchb = (kg.nz + CHB - 1) / CHB;
+        dim3 gridb((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchb);
         float2 *pref = reinterpret_cast<float2 *>(pref_ws);
         dim3 sg((kg.nu + 255) / 256, n_views_total);
         if (scaled)
@@ -556,13 +560,13 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
         TNLM_TRY_CUDA(cudaGetLastError());
         const size_t smem = sizeof(float4) * kg.nv;
         if (smem > 48 * 1024) {
-            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<false, CHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
         if (scaled)
-            k_backproject_bands<true><<<grid, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchunks);
+            k_backproject_bands<true, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchb);
         else
-            k_backproject_bands<false><<<grid, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchunks);
+            k_backproject_bands<false, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchb);
         TNLM_TRY_CUDA(cudaGetLastError());
         return TNLM_OK;
     }

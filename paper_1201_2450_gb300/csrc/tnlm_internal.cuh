@@ -82,6 +82,27 @@ tnlm_status launch_normalize(float *x, long long n, const double *nrm2, cudaStre
 
 int sumsq_scratch_len();
 
+// CGLS for (P1) with per-phase scalars (cgls.cu).
+struct CglsArgs {
+    const KGeom *kg;
+    const ViewGeom *views;
+    const int *view_off;
+    int n_views_total;
+    const float *y;          // projections
+    float *x;                // iterate (in/out), np * nvox
+    float *r, *q;            // projection-sized scratch
+    float *s, *p;            // volume-sized scratch
+    float *pref;             // transpose prefix workspace (nullable)
+    const long long *vseg;   // [np+1] element offsets of the phases in a volume
+    const long long *pseg;   // [np+1] element offsets of the phases in a projection set
+    double *scal;            // 3 * np scalars
+    double *partial;         // max(cgls_partial_len(np), sumsq_scratch_len()) doubles
+    double *report_dev;      // nullable, [n_iter + 1] residual norms
+    int n_iter;
+};
+tnlm_status run_cgls(const CglsArgs &a, cudaStream_t st);
+int cgls_partial_len(int np);
+
 tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float h, float mu);
 
 }  // namespace tnlm
@@ -104,6 +125,14 @@ struct tnlm_geometry {
     long long part_len = 0;
     double *d_scalars = nullptr;      // reduction results
     float *d_pref = nullptr;          // column prefix sums for the transpose (prefix_floats)
+    // CGLS workspace (allocated on first use)
+    float *d_q = nullptr;             // sum(n_views) * npix
+    float *d_s = nullptr;             // np * nvox
+    float *d_p = nullptr;             // np * nvox
+    long long *d_vseg = nullptr;      // [np+1]
+    long long *d_pseg = nullptr;      // [np+1]
+    double *d_cscal = nullptr;        // 3 * np
+    double *d_cpart = nullptr;        // CGLS reduction partials
     long long scalars_len = 0;
     // instrumentation
     int timing = 0;

@@ -356,3 +356,51 @@ def test_full_size_fused_iteration_equals_composed_calls(c2_full):
     g = tnlm.tnlm_backproject(G, r.contiguous(), f0.clone(), alpha=-tau, beta=1.0)
     f2 = tnlm.tnlm_gauss_jacobi(g, g, g, cfg.d, cfg.M, cfg.h, cfg.mu, 1)
     assert rel_l2(f.cpu().numpy(), f2.cpu().numpy()) <= RTOL
+
+
+@pytest.mark.parametrize("gj_start,n_gj", [(0, 2), (0, 3), (1, 1), (1, 3)])
+def test_reconstruct_multi_sweep_p2(ora, gj_start, n_gj):
+    """(P2) with n_gj Eq. 8 iterations (weights of g^(k) frozen) against the oracle."""
+    geom = GEOMS["ragged_uneven"]
+    OG = ora.Geometry(geom)
+    G = tnlm.Geometry(geom)
+    y = synth.uniform(G.proj_shape, 180) * 0.5
+    f0 = synth.smooth_volume(G.vol_shape, 181)
+    tau = 1e-4
+    ref = ora.reconstruct(OG, y, f0, tau, 1, 2, 0.02, 0.7, 2, clip=1, gj_start=gj_start, n_gj=n_gj)
+    f = cuda(f0)
+    tnlm.tnlm_reconstruct(G, cuda(y), f, tnlm.Params(d=1, M=2, h=0.02, mu=0.7, tau=tau, n_outer=2, clip_nonneg=1,
+                                                     gj_start=gj_start, n_gj=n_gj))
+    assert rel_l2(f.cpu().numpy(), ref) <= RTOL
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_cgls_matches_oracle(ora, name):
+    """(P1) by CGLS with per-phase scalars against the FP64 oracle."""
+    geom = GEOMS[name]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    x_true = synth.smooth_volume(G.vol_shape, 190)
+    y = ora.project(OG, x_true) + synth.normal(G.proj_shape, 191, 1e-3)
+    x0 = synth.smooth_volume(G.vol_shape, 192) * 0.5
+    ref, rep_ref = ora.cgls(OG, y, x0, 4, with_report=True)
+    x = cuda(x0)
+    _, rep = tnlm.tnlm_cgls(G, cuda(y), x, 4, report=True)
+    assert rel_l2(x.cpu().numpy(), ref) <= RTOL
+    np.testing.assert_allclose(rep, rep_ref, rtol=1e-4)
+    assert np.all(np.diff(rep) <= 0)
+
+
+def test_reconstruct_with_cgls_matches_oracle(ora):
+    cfg = synth.C1
+    pb = synth.recon_problem(cfg)
+    OG = ora.Geometry(pb.geom)
+    y = pb.y.numpy()
+    ref, rep_ref = ora.reconstruct(OG, y, np.zeros(OG.vol_shape), 0.0, cfg.d, cfg.M, cfg.h, cfg.mu, 2, n_inner=3,
+                                   p1_cgls=1, with_report=True)
+    G = tnlm.Geometry(pb.geom)
+    f = torch.zeros(G.vol_shape, device="cuda")
+    _, rep = tnlm.tnlm_reconstruct(G, cuda(y), f, tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, n_outer=2,
+                                                              n_inner=3, p1_solver=1), report=True)
+    assert rel_l2(f.cpu().numpy(), ref) <= RTOL
+    np.testing.assert_allclose(rep, rep_ref, rtol=1e-4)

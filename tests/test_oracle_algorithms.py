@@ -74,3 +74,63 @@ def test_enhance_constant_and_noise_reduction(ora):
     g = clean + synth.normal(shape, 49, 0.002)
     f = ora.enhance(g, 1, 2, 0.01, 1.0, 5)
     assert np.linalg.norm(f - clean) < 0.8 * np.linalg.norm(g - clean)
+
+
+def test_reconstruct_multi_sweep_p2(ora):
+    """n_gj Eq. 8 iterations per (P2) with the weights of g^(k) frozen, the
+    positivity correction after the last one."""
+    geom, truth, y = _small_problem(50)
+    G = ora.Geometry(geom)
+    tau, d, M, h, mu = 0.01, 1, 1, 0.05, 0.8
+    f0 = truth.astype(np.float64)
+    for gj_start in (0, 1):
+        f = ora.reconstruct(G, y, f0, tau, d, M, h, mu, n_outer=1, n_gj=3, clip=1, gj_start=gj_start)
+        g = f0 - tau * ora.backproject(G, ora.project(G, f0) - y)
+        w = ora.weights(g, d, M, h)
+        fl = f0.copy() if gj_start else g.copy()
+        for l in range(3):
+            fl = ora.gj_apply(w, M, fl, g, mu, clip=1 if l == 2 else 0)
+        np.testing.assert_allclose(f, fl, rtol=1e-12, atol=1e-15)
+
+
+def test_cgls_reaches_least_squares_and_is_phase_separable(ora):
+    """CGLS (ref. 37) on an overdetermined tiny problem reaches the dense
+    least-squares solution; residuals never grow; running it on all phases at
+    once equals running it on each phase alone (Sec. 2.3: (P1) is uncoupled)."""
+    geom = synth.make_geometry(nx=4, ny=4, nz=3, dx=1.0, nu=10, nv=6, du=1.2, sad=30, sdd=45, n_phases=2,
+                               views_per_phase=[5, 4], angle_offset=0.1)
+    G = ora.Geometry(geom)
+    x_true = synth.smooth_volume(G.vol_shape, 60).astype(np.float64)
+    y = ora.project(G, x_true) + synth.normal(G.proj_shape, 61, 1e-3)
+    x, rep = ora.cgls(G, y, np.zeros(G.vol_shape), 200, with_report=True)
+    assert np.all(np.diff(rep) <= 1e-12 * rep[0])
+    # dense least squares per phase
+    nvox = 48
+    for ph, (v0, v1) in enumerate(((0, 5), (5, 9))):
+        sub = dict(geom)
+        sub["nviews"] = np.array([v1 - v0], np.int32)
+        sub["angles"] = np.asarray(geom["angles"][v0:v1])
+        Gs = ora.Geometry(sub)
+        cols = []
+        for v in range(nvox):
+            e = np.zeros((1, 3, 4, 4))
+            e.reshape(-1)[v] = 1.0
+            cols.append(ora.project(Gs, e).ravel())
+        P = np.stack(cols, 1)
+        x_ls = np.linalg.lstsq(P, y[v0:v1].ravel(), rcond=None)[0]
+        np.testing.assert_allclose(x[ph].ravel(), x_ls, rtol=1e-6, atol=1e-8)
+        # a few iterations on the phase alone equal the joint run's iterates
+        xa = ora.cgls(Gs, y[v0:v1], np.zeros((1, 3, 4, 4)), 5)
+        xj = ora.cgls(G, y, np.zeros(G.vol_shape), 5)
+        np.testing.assert_allclose(xj[ph], xa[0], rtol=1e-11, atol=1e-14)
+
+
+def test_reconstruct_with_cgls_p1(ora):
+    geom, truth, y = _small_problem(62)
+    G = ora.Geometry(geom)
+    d, M, h, mu = 1, 1, 0.05, 0.8
+    f0 = truth.astype(np.float64)
+    f, rep = ora.reconstruct(G, y, f0, 0.0, d, M, h, mu, n_outer=1, n_inner=3, p1_cgls=1, with_report=True)
+    g, crep = ora.cgls(G, y, f0, 3, with_report=True)
+    np.testing.assert_allclose(rep[0], crep[:3], rtol=1e-12)
+    np.testing.assert_allclose(f, ora.gj_sweep(g, g, g, d, M, h, mu, 1), rtol=1e-12, atol=1e-15)
