@@ -289,6 +289,8 @@ def run_ours(args, rank, world, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = e_steps * world / e2e_s
 
+    variants = {} if args.no_variants else measure_variants(tnlm, synth, geom, y, stream)
+
     peaks = measured_peaks()
     names = ["k_forward", "k_backproject", "k_sweep"]
     per_launch_ms = {n: stage_ms[k] / max(stage_n[k], 1) for k, n in enumerate(names)}
@@ -339,12 +341,57 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(sum(stage_n)),
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
+        "variants": variants,
     }
     if args.phases != 10:
         line["config"]["workload"] += f" [reduced to {args.phases} phases]"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(cfg, pb)
     return line
+
+
+def _time_ms(fn, stream, reps=3):
+    """Median CUDA-event time of fn() on `stream` over reps runs (after one warm-up)."""
+    fn()
+    out = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def measure_variants(tnlm, synth, geom, y, stream) -> dict:
+    """Steps either side of the FBS iteration and the enhancement workload:
+    FDK of all phases, one CGLS iteration of (P1), and TNLM-E on
+    10 x 512x512x128 (d = 2, M = 3, h = 0.04) in FP32."""
+    out = {}
+    vol = torch.empty(geom.vol_shape, device="cuda")
+    out["fdk_ms"] = round(_time_ms(lambda: tnlm.tnlm_fdk(geom, y, vol), stream), 3)
+    x = torch.zeros(geom.vol_shape, device="cuda")
+    n_it = 3
+    ms = _time_ms(lambda: tnlm.tnlm_cgls(geom, y, x, n_it), stream)
+    x0 = torch.zeros(geom.vol_shape, device="cuda")
+    ms0 = _time_ms(lambda: tnlm.tnlm_cgls(geom, y, x0, 0), stream)
+    out["cgls_ms_per_iteration"] = round((ms - ms0) / n_it, 3)
+    out["cgls_setup_ms"] = round(ms0, 3)
+    c3 = synth.C3
+    g, _ = synth.enhance_input(c3, device="cuda")
+    f = torch.empty_like(g)
+    p = tnlm.Params(d=c3.d, M=c3.M, h=c3.h, mu=c3.mu, n_outer=1, clip_nonneg=0)
+    sweep_ms = _time_ms(lambda: tnlm.tnlm_enhance(g, p, out=f), stream, reps=2)
+    nvox = c3.n_phases * c3.vol[0] * c3.vol[1] * c3.vol[2]
+    out["tnlm_e_workload"] = "TNLM-E FP32 10 x 512x512x128, patch 5^3, window 7^3, h 0.04, mu 1"
+    out["tnlm_e_ms_per_sweep"] = round(sweep_ms, 3)
+    out["tnlm_e_voxel_updates_per_s"] = round(nvox / (sweep_ms / 1e3), 1)
+    out["tnlm_e_pair_evals_per_s"] = round(sweep_pairs(c3) / (sweep_ms / 1e3), 1)
+    del g, f
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -418,6 +465,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", type=int, default=10, help="phases of the workload (10; fewer for profiling)")
     ap.add_argument("--power-iters", type=int, default=20, help="power iterations that size the step tau")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FDK / CGLS / TNLM-E measurements")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -183,6 +183,19 @@ tnlm_status tnlm_enhance_noalloc(int nx, int ny, int nz, int n_phases, const flo
  * allocates CGLS workspace in the handle (two volumes, one projection set). */
 tnlm_status tnlm_cgls(tnlm_geometry *geom, const float *y, float *x, int n_iter, double *report, void *stream);
 
+/* FDK reconstruction (Feldkamp, Davis and Kress, the paper's ref. 16), the
+ * initial value f^(0) of TNLM-R and the input g of TNLM-E (Sec. 2.2-2.3):
+ * every phase from its own views, assumed to cover a full rotation evenly
+ * (step 2 pi / n_views[i]).  Projections are cosine-weighted by
+ * SDD / sqrt(SDD^2 + u^2 + v^2), filtered along u with the discrete ramp
+ * kernel h[0] = 1/(4 du^2), h[odd m] = -1/(m^2 pi^2 du^2), h[even] = 0, and
+ * back-projected voxel by voxel with bilinear interpolation (zero outside the
+ * detector) and weight (2 pi / n_views[i]) / 2 * SAD SDD / U^2.
+ * proj: [sum n_views][nv][nu]; vol: [N_p][nz][ny][nx] (overwritten).
+ * Uses the handle's projection-sized workspace (allocated on first use).
+ * TNLM_ERR_ARG if nz * N_p > 65535 or nu > 8192. */
+tnlm_status tnlm_fdk(tnlm_geometry *geom, const float *proj, float *vol, void *stream);
+
 /* Estimate L = ||P||_2^2 (so tau = 1/L for the (P1) step) by n_iter power
  * iterations on P^T P from the start image x ([N_p][nz][ny][nx], device,
  * overwritten).  *L_out (host) receives the Rayleigh quotient ||P x||^2 of

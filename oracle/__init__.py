@@ -81,6 +81,7 @@ def _load():
             "ora_fidelity": (d, [G, _dp, _dp]),
             "ora_reconstruct": (None, [G, _dp, _dp, d, i, i, d, d, i, i, i, i, i, i, C.c_void_p]),
             "ora_cgls": (None, [G, _dp, _dp, i, C.c_void_p]),
+            "ora_fdk": (None, [G, _dp, _dp, C.c_void_p]),
             "ora_enhance": (None, [i, i, i, i, _dp, _dp, i, i, d, d, i, i]),
             "ora_num_threads": (i, []),
         }
@@ -232,6 +233,15 @@ def cgls(geom: Geometry, y, x0, n_iter: int, with_report: bool = False):
     _load().ora_cgls(geom.ref, _f64(y).reshape(geom.proj_shape), x, n_iter,
                      rep.ctypes.data if rep is not None else None)
     return (x, rep) if with_report else x
+
+
+def fdk(geom: Geometry, proj, with_filtered: bool = False):
+    """FDK of every phase from its own views (full-scan, ref. 16)."""
+    out = np.empty(geom.vol_shape, np.float64)
+    filt = np.empty(geom.proj_shape, np.float64) if with_filtered else None
+    _load().ora_fdk(geom.ref, _f64(proj).reshape(geom.proj_shape), out,
+                    filt.ctypes.data if filt is not None else None)
+    return (out, filt) if with_filtered else out
 
 
 def enhance(g, d: int, M: int, h: float, mu: float, n_sweeps: int, clip: int = 0) -> np.ndarray:

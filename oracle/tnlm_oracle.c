@@ -51,7 +51,11 @@
  * (ix - (nx-1)/2) dx + cx, ... .  Volumes are [np][nz][ny][nx] (x fastest),
  * projections [sum of views][nv][nu] (u fastest), views grouped by phase.
  */
+#define _USE_MATH_DEFINES
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -601,6 +605,78 @@ void ora_cgls(const ora_geom *g, const double *yproj, double *x, int n_iter, dou
     free(p);
     free(gam);
     free(pofs);
+}
+
+/* FDK (Feldkamp, Davis and Kress, the paper's ref. 16), the initial value of
+ * TNLM-R and the input of TNLM-E (Sec. 2.2-2.3), for each phase from its own
+ * views, assumed to cover a full rotation evenly (d_theta = 2 pi / V_i):
+ *   R'(u,v) = R(u,v) SDD / sqrt(SDD^2 + u^2 + v^2)              (cosine weight)
+ *   F(u_n,v) = du sum_k h[n-k] R'(u_k,v),  h[0] = 1/(4 du^2), h[even] = 0,
+ *              h[odd m] = -1/(m^2 pi^2 du^2)                        (ramp filter)
+ *   f(x)    = sum_views d_theta/2 * SAD SDD / U^2 * F(u(x), v(x)),
+ * U = SAD - (x cos t + y sin t), u = SDD (-x sin t + y cos t)/U, v = SDD z/U,
+ * F bilinear in (u, v) and zero outside the detector.  filt (nullable)
+ * receives F, [sum n_views][nv][nu]. */
+void ora_fdk(const ora_geom *g, const double *proj, double *vol, double *filt)
+{
+    const int nvt = ora_total_views(g);
+    const long npix = ora_npix(g), nvox = ora_nvox(g);
+    double *F = (double *)malloc(sizeof(double) * nvt * npix);
+#pragma omp parallel for schedule(static)
+    for (long row = 0; row < (long)nvt * g->nv; ++row) {
+        const int iv = (int)(row % g->nv);
+        const double v = (iv - 0.5 * (g->nv - 1)) * g->dv + g->v_off;
+        const double *pr = proj + row * g->nu;
+        double *fr = F + row * g->nu;
+        for (int n = 0; n < g->nu; ++n) {
+            double acc = 0.0;
+            for (int k = 0; k < g->nu; ++k) {
+                const int m = n - k;
+                double h;
+                if (m == 0)
+                    h = 1.0 / (4.0 * g->du * g->du);
+                else if (m % 2 == 0)
+                    h = 0.0;
+                else
+                    h = -1.0 / ((double)m * m * M_PI * M_PI * g->du * g->du);
+                const double u = (k - 0.5 * (g->nu - 1)) * g->du + g->u_off;
+                acc += h * pr[k] * g->sdd / sqrt(g->sdd * g->sdd + u * u + v * v);
+            }
+            fr[n] = g->du * acc;
+        }
+    }
+    if (filt) memcpy(filt, F, sizeof(double) * nvt * npix);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int ph = 0; ph < g->np; ++ph)
+        for (long vx = 0; vx < nvox; ++vx) {
+            const int ix = (int)(vx % g->nx), iy = (int)((vx / g->nx) % g->ny), iz = (int)(vx / ((long)g->nx * g->ny));
+            const double x = g->cx + (ix - 0.5 * (g->nx - 1)) * g->dx;
+            const double y = g->cy + (iy - 0.5 * (g->ny - 1)) * g->dy;
+            const double z = g->cz + (iz - 0.5 * (g->nz - 1)) * g->dz;
+            const int v0 = ora_first_view(g, ph);
+            const double dth = 2.0 * M_PI / g->nviews[ph];
+            double acc = 0.0;
+            for (int vg = v0; vg < v0 + g->nviews[ph]; ++vg) {
+                const double c = cos(g->angles[vg]), sn = sin(g->angles[vg]);
+                const double U = g->sad - (x * c + y * sn);
+                const double u = g->sdd * (-x * sn + y * c) / U;
+                const double v = g->sdd * z / U;
+                const double fu = (u - g->u_off) / g->du + 0.5 * (g->nu - 1);
+                const double fv = (v - g->v_off) / g->dv + 0.5 * (g->nv - 1);
+                const int iu0 = (int)floor(fu), iv0 = (int)floor(fv);
+                const double au = fu - iu0, av = fv - iv0;
+                double val = 0.0;
+                for (int dv_ = 0; dv_ < 2; ++dv_)
+                    for (int du_ = 0; du_ < 2; ++du_) {
+                        const int iu = iu0 + du_, iv = iv0 + dv_;
+                        if (iu < 0 || iu >= g->nu || iv < 0 || iv >= g->nv) continue;
+                        val += (du_ ? au : 1.0 - au) * (dv_ ? av : 1.0 - av) * F[(long)vg * npix + (long)iv * g->nu + iu];
+                    }
+                acc += 0.5 * dth * g->sad * g->sdd / (U * U) * val;
+            }
+            vol[(long)ph * nvox + vx] = acc;
+        }
+    free(F);
 }
 
 /* TNLM-R: f holds f^(0) on entry and the result on exit.  report (nullable)

@@ -27,7 +27,7 @@ from ._build import build
 __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
-    "tnlm_operator_norm", "tnlm_cgls",
+    "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk",
     "reconstruct_host", "library_path",
 ]
 
@@ -112,6 +112,7 @@ def _load():
             "tnlm_enhance_noalloc": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
             "tnlm_cgls": (i, [vp, vp, vp, i, vp, vp]),
+            "tnlm_fdk": (i, [vp, vp, vp, vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
             "tnlm_status_string": (C.c_char_p, [i]),
@@ -296,6 +297,15 @@ def tnlm_cgls(geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, rep
                              _dev(x, "x", geom.device, geom.vol_shape), n_iter,
                              rep.ctypes.data if rep is not None else None, _stream(stream)), "tnlm_cgls")
     return x, rep
+
+
+def tnlm_fdk(geom: Geometry, proj: torch.Tensor, vol: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """FDK of every phase from its own views (full rotation, ref. 16)."""
+    if vol is None:
+        vol = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+    _check(_load().tnlm_fdk(geom.handle, _dev(proj, "proj", geom.device, geom.proj_shape),
+                            _dev(vol, "vol", geom.device, geom.vol_shape), _stream(stream)), "tnlm_fdk")
+    return vol
 
 
 def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:

@@ -496,6 +496,16 @@ tnlm_status tnlm_cgls(tnlm_geometry *geo, const float *y, float *x, int n_iter, 
     return TNLM_OK;
 }
 
+tnlm_status tnlm_fdk(tnlm_geometry *geo, const float *proj, float *vol, void *stream)
+{
+    if (!geo || !proj || !vol) return arg_error("geometry, proj and vol must not be NULL");
+    const KGeom &kg = geo->kg;
+    if ((long long)kg.nz * kg.np > 65535) return arg_error("tnlm_fdk needs nz * n_phases <= 65535");
+    if (kg.nu > 8192) return arg_error("tnlm_fdk needs nu <= 8192");
+    TNLM_TRY(dev_alloc(&geo->d_r, (size_t)geo->n_views_total * kg.npix));
+    return launch_fdk(kg, geo->d_views, geo->d_view_off, geo->n_views_total, proj, geo->d_r, vol, as_stream(stream));
+}
+
 tnlm_status tnlm_set_stage_timing(tnlm_geometry *g, int enable)
 {
     if (!g) return arg_error("geometry must not be NULL");

@@ -101,6 +101,10 @@ struct CglsArgs {
     int n_iter;
 };
 tnlm_status run_cgls(const CglsArgs &a, cudaStream_t st);
+
+// FDK of every phase from its own views (fdk.cu); filt: projection-sized scratch.
+tnlm_status launch_fdk(const KGeom &kg, const ViewGeom *views, const int *view_off, int n_views_total,
+                       const float *proj, float *filt, float *vol, cudaStream_t st);
 int cgls_partial_len(int np);
 
 tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float h, float mu);

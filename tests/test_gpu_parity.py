@@ -404,3 +404,17 @@ def test_reconstruct_with_cgls_matches_oracle(ora):
                                                               n_inner=3, p1_solver=1), report=True)
     assert rel_l2(f.cpu().numpy(), ref) <= RTOL
     np.testing.assert_allclose(rep, rep_ref, rtol=1e-4)
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_fdk_matches_oracle(ora, name):
+    """FDK (ref. 16) of every phase against the FP64 oracle."""
+    geom = GEOMS[name]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    objs = [[((1.0, -0.5, 0.3), (6.0, 5.0, 3.0), 0.02), ((-2.0, 1.0, 0.0), (2.0, 2.0, 2.0), 0.01)]
+            for _ in range(G.np)]
+    p = synth.analytic_projections(geom, objs).numpy() + synth.normal(G.proj_shape, 200, 1e-3)
+    ref = ora.fdk(OG, p)
+    out = tnlm.tnlm_fdk(G, cuda(p)).cpu().numpy()
+    assert rel_l2(out, ref) <= RTOL
