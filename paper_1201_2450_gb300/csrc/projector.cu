@@ -348,8 +348,10 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
 // ray-length-scaled projection, accumulated in FP64 and stored as an
 // (hi, lo) float pair: pref[vg][iv][iu] = sum_{t < iv} r(t) |D(t)|.  A sum over
 // a run of rows is then two loads and a difference, exact to FP32 rounding.
+// For an unscaled input the scaled values are also written to scaled_out.
 template <bool SCALED>
-__global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restrict__ proj, float2 *__restrict__ pref)
+__global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restrict__ proj, float2 *__restrict__ pref,
+                                                 float *__restrict__ scaled_out)
 {
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
     const int vg = blockIdx.y;
@@ -357,14 +359,16 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
     const float u = ((float)iu - G.uc) * G.du + G.u_off;
     const float len_u2 = G.sdd * G.sdd + u * u;
     const float *__restrict__ pc = proj + (long long)vg * G.npix + iu;
+    float *__restrict__ so = SCALED ? nullptr : scaled_out + (long long)vg * G.npix + iu;
     float2 *__restrict__ po = pref + (long long)vg * (G.nv + 1) * G.nu + iu;
     double acc = 0.0;
     po[0] = make_float2(0.f, 0.f);
     for (int iv = 0; iv < G.nv; ++iv) {
         float r = __ldg(pc + (long long)iv * G.nu);
-        if (!SCALED) {
+        if (!SCALED) {  // scale by the ray length once, for the band rows too
             const float v = ((float)iv - G.vc) * G.dv + G.v_off;
             r *= sqrtf(len_u2 + v * v);
+            so[(long long)iv * G.nu] = r;
         }
         acc += (double)r;
         const float hi = (float)acc;
@@ -537,7 +541,8 @@ bool bands_apply(const KGeom &kg)
 
 size_t prefix_floats(const KGeom &kg, int n_views_total)
 {
-    return (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu;
+    // (hi, lo) prefix sums plus a ray-length-scaled copy of an unscaled input
+    return (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu + (size_t)n_views_total * kg.npix;
 }
 
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
@@ -552,21 +557,18 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
         const int nchb = (kg.nz + CHB - 1) / CHB;
         dim3 gridb((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchb);
         float2 *pref = reinterpret_cast<float2 *>(pref_ws);
+        float *rtil = pref_ws + (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu;  // unscaled input: r |D| copy
         dim3 sg((kg.nu + 255) / 256, n_views_total);
         if (scaled)
-            k_colscan<true><<<sg, 256, 0, st>>>(kg, proj, pref);
+            k_colscan<true><<<sg, 256, 0, st>>>(kg, proj, pref, nullptr);
         else
-            k_colscan<false><<<sg, 256, 0, st>>>(kg, proj, pref);
+            k_colscan<false><<<sg, 256, 0, st>>>(kg, proj, pref, rtil);
         TNLM_TRY_CUDA(cudaGetLastError());
         const size_t smem = sizeof(float4) * kg.nv;
-        if (smem > 48 * 1024) {
+        if (smem > 48 * 1024)
             TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<false, CHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        }
-        if (scaled)
-            k_backproject_bands<true, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchb);
-        else
-            k_backproject_bands<false, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, proj, pref, vin, vout, alpha, beta, nchb);
+        k_backproject_bands<true, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, scaled ? proj : rtil, pref, vin,
+                                                                    vout, alpha, beta, nchb);
         TNLM_TRY_CUDA(cudaGetLastError());
         return TNLM_OK;
     }
