@@ -389,7 +389,12 @@ def measure_variants(tnlm, synth, geom, y, stream) -> dict:
     out["tnlm_e_ms_per_sweep"] = round(sweep_ms, 3)
     out["tnlm_e_voxel_updates_per_s"] = round(nvox / (sweep_ms / 1e3), 1)
     out["tnlm_e_pair_evals_per_s"] = round(sweep_pairs(c3) / (sweep_ms / 1e3), 1)
-    del g, f
+    gb = g.to(torch.bfloat16)
+    fb = torch.empty_like(gb)
+    bf_ms = _time_ms(lambda: tnlm.tnlm_enhance_bf16(gb, p, out=fb), stream, reps=2)
+    out["tnlm_e_bf16_ms_per_sweep"] = round(bf_ms, 3)
+    out["tnlm_e_bf16_voxel_updates_per_s"] = round(nvox / (bf_ms / 1e3), 1)
+    del g, f, gb, fb
     torch.cuda.empty_cache()
     return out
 

@@ -31,6 +31,7 @@
 #define TNLM_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -150,6 +151,19 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, cons
  * N_p nx ny nz float buffer stream-ordered (cudaMallocAsync) per call. */
 tnlm_status tnlm_enhance(int nx, int ny, int nz, int n_phases, const float *g, float *f, const tnlm_params *params,
                          void *stream);
+
+/* BF16 storage with FP32 arithmetic (the images are stored as bfloat16 bit
+ * patterns; they are widened to FP32 when read, every patch distance,
+ * weight, normaliser and Eq. 8 combination is FP32, and the output is
+ * rounded to nearest bfloat16).  Same operation and argument rules as
+ * tnlm_gauss_jacobi (one Eq. 8 sweep with the Eq. 9 weights of wsrc) and
+ * tnlm_enhance (TNLM-E, Sec. 2.3); available for d in {1,2} and M in {1,2,3}
+ * (TNLM_ERR_NOT_IMPLEMENTED otherwise). */
+tnlm_status tnlm_gauss_jacobi_bf16(int nx, int ny, int nz, int n_phases, const uint16_t *wsrc, const uint16_t *vals,
+                                   const uint16_t *g, uint16_t *f_out, int d, int M, float h, float mu, int clip,
+                                   void *stream);
+tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int n_phases, const uint16_t *g, uint16_t *f,
+                              const tnlm_params *params, void *stream);
 
 /* TNLM-E without any device allocation, for callers that cannot allocate
  * device memory (e.g. an application whose memory pool owns the GPU's

@@ -27,7 +27,7 @@ from ._build import build
 __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
-    "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk",
+    "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
     "reconstruct_host", "library_path",
 ]
 
@@ -113,6 +113,8 @@ def _load():
             "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
             "tnlm_cgls": (i, [vp, vp, vp, i, vp, vp]),
             "tnlm_fdk": (i, [vp, vp, vp, vp]),
+            "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
             "tnlm_status_string": (C.c_char_p, [i]),
@@ -140,11 +142,12 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _dev(t: torch.Tensor, name: str, device: torch.device | None = None, shape=None) -> int:
+def _dev(t: torch.Tensor, name: str, device: torch.device | None = None, shape=None,
+         dtype=torch.float32) -> int:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
-    if t.dtype != torch.float32:
-        raise ValueError(f"{name} must be float32")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if device is not None and t.device != device:
@@ -306,6 +309,32 @@ def tnlm_fdk(geom: Geometry, proj: torch.Tensor, vol: torch.Tensor | None = None
     _check(_load().tnlm_fdk(geom.handle, _dev(proj, "proj", geom.device, geom.proj_shape),
                             _dev(vol, "vol", geom.device, geom.vol_shape), _stream(stream)), "tnlm_fdk")
     return vol
+
+
+def tnlm_gauss_jacobi_bf16(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d: int, M: int, h: float,
+                           mu: float, clip: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One Eq. 8 sweep on bfloat16 images with FP32 arithmetic."""
+    np_, nz, ny, nx = wsrc.shape
+    if out is None:
+        out = torch.empty_like(wsrc)
+    bf, dev = torch.bfloat16, wsrc.device
+    _check(_load().tnlm_gauss_jacobi_bf16(nx, ny, nz, np_, _dev(wsrc, "wsrc", dtype=bf),
+                                          _dev(vals, "vals", dev, wsrc.shape, bf), _dev(g, "g", dev, wsrc.shape, bf),
+                                          _dev(out, "f_out", dev, wsrc.shape, bf), d, M, h, mu, int(clip),
+                                          _stream(stream)), "tnlm_gauss_jacobi_bf16")
+    return out
+
+
+def tnlm_enhance_bf16(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """TNLM-E on bfloat16 images with FP32 arithmetic."""
+    np_, nz, ny, nx = g.shape
+    if out is None:
+        out = torch.empty_like(g)
+    p = params._c()
+    bf = torch.bfloat16
+    _check(_load().tnlm_enhance_bf16(nx, ny, nz, np_, _dev(g, "g", dtype=bf), _dev(out, "f", g.device, g.shape, bf),
+                                     C.byref(p), _stream(stream)), "tnlm_enhance_bf16")
+    return out
 
 
 def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:

@@ -459,6 +459,48 @@ tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *
     return s;
 }
 
+tnlm_status tnlm_gauss_jacobi_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
+                                   const uint16_t *g, uint16_t *f_out, int d, int M, float h, float mu, int clip,
+                                   void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, mu));
+    if (!wsrc || !vals || !g || !f_out) return arg_error("wsrc, vals, g and f_out must not be NULL");
+    if (f_out == wsrc || f_out == vals || f_out == g) return arg_error("f_out must not alias wsrc, vals or g");
+    return launch_sweep_bf16(nx, ny, nz, np, wsrc, vals, g, f_out, d, M, h, mu, clip, as_stream(stream));
+}
+
+tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int np, const uint16_t *g, uint16_t *f, const tnlm_params *p,
+                              void *stream)
+{
+    TNLM_TRY(check_params(p, false));
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, p->d, p->M, p->h, p->mu));
+    if (!g || !f) return arg_error("g and f must not be NULL");
+    if (g == f) return arg_error("g and f must not alias");
+    cudaStream_t st = as_stream(stream);
+    const size_t n = (size_t)np * nx * ny * nz;
+    if (p->n_outer == 0) {
+        TNLM_TRY_CUDA(cudaMemcpyAsync(f, g, sizeof(uint16_t) * n, cudaMemcpyDeviceToDevice, st));
+        return TNLM_OK;
+    }
+    uint16_t *tmp = nullptr;
+    if (p->n_outer > 1) {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint16_t) * n, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMallocAsync of the BF16 ping-pong buffer (%zu bytes) failed", sizeof(uint16_t) * n);
+            return TNLM_ERR_OOM;
+        }
+    }
+    const uint16_t *src = g;
+    tnlm_status s = TNLM_OK;
+    for (int k = 0; k < p->n_outer && s == TNLM_OK; ++k) {
+        uint16_t *dst = ((p->n_outer - 1 - k) % 2 == 0) ? f : tmp;
+        s = launch_sweep_bf16(nx, ny, nz, np, src, src, g, dst, p->d, p->M, p->h, p->mu, p->clip_nonneg, st);
+        src = dst;
+    }
+    if (tmp) cudaFreeAsync(tmp, st);
+    return s;
+}
+
 tnlm_status tnlm_operator_norm(tnlm_geometry *geo, float *x, int n_iter, double *L_out, void *stream)
 {
     if (!geo || !x || !L_out) return arg_error("geometry, x and L_out must not be NULL");

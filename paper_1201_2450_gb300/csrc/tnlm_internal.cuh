@@ -72,6 +72,9 @@ tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, cons
                          float *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
 tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,
                            cudaStream_t st);
+// BF16 images (bit patterns), FP32 arithmetic; box configurations only
+tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
+                              const uint16_t *g, uint16_t *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
 
 // FP64 reductions: *result = sum(partials[0..n)); sum of squares of x.
 tnlm_status launch_sum_partials(const double *partials, long long n, double *result, cudaStream_t st);

@@ -11,6 +11,8 @@
 // 2^(m - t) / sum 2^(m - t) for any reference m, and the reference only moves
 // (rescaling the running sums) when a candidate beats it by more than
 // kRescale, so no weight overflows and the largest weight is >= 1.
+#include <cuda_bf16.h>
+
 #include <cfloat>
 #include <cmath>
 
@@ -31,16 +33,24 @@ __device__ __forceinline__ float ex2(float x)
 
 __device__ __forceinline__ int clampi(int a, int n) { return a < 0 ? 0 : (a >= n ? n - 1 : a); }
 
+// Storage types of the images: FP32, or BF16 (widened to FP32 on load; every
+// sum, weight and normaliser stays FP32; the output is rounded to BF16).
+__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
 // Stage the box [o0, o0 + ext) of one phase image into shared memory with
 // coordinates clamped to the volume.
-__device__ __forceinline__ void stage_clamped(float *dst, const float *__restrict__ src, int ox, int oy, int oz,
+template <class T>
+__device__ __forceinline__ void stage_clamped(float *dst, const T *__restrict__ src, int ox, int oy, int oz,
                                               int ex, int ey, int ez, int nx, int ny, int nz, int tid, int nthr)
 {
     const int n = ex * ey * ez;
     for (int t = tid; t < n; t += nthr) {
         const int lx = t % ex, ly = (t / ex) % ey, lz = t / (ex * ey);
         const int gx = clampi(ox + lx, nx), gy = clampi(oy + ly, ny), gz = clampi(oz + lz, nz);
-        dst[t] = __ldg(src + ((long long)gz * ny + gy) * nx + gx);
+        dst[t] = ld(src + ((long long)gz * ny + gy) * nx + gx);
     }
 }
 
@@ -303,10 +313,10 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
     }
 }
 
-template <int D_, int M_, int BY, int BZ>
+template <int D_, int M_, int BY, int BZ, class T>
 __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
-    k_sweep_box(int nx, int ny, int nz, int np, int ntx, int nty, int ntz, const float *__restrict__ wsrc,
-                const float *__restrict__ vals, const float *__restrict__ g, float *__restrict__ out, float c2,
+    k_sweep_box(int nx, int ny, int nz, int np, int ntx, int nty, int ntz, const T *__restrict__ wsrc,
+                const T *__restrict__ vals, const T *__restrict__ g, T *__restrict__ out, float c2,
                 float mu, int clip)
 {
     using C = BoxCfg<D_, M_, BY, BZ>;
@@ -332,15 +342,15 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
     // this thread's patch block of phase i (clamped reads) as [z][y pair], kept for all offsets
     float2 ai[C::SZ][C::SY / 2];
     {
-        const float *src = wsrc + i * nvox;
+        const T *src = wsrc + i * nvox;
         const int cx = clampi(x, nx);
 #pragma unroll
         for (int zz = 0; zz < C::SZ; ++zz)
 #pragma unroll
             for (int p = 0; p < C::SY / 2; ++p) {
                 const long long zo = (long long)clampi(zb - D_ + zz, nz) * ny;
-                ai[zz][p] = make_float2(__ldg(src + (zo + clampi(yb - D_ + 2 * p, ny)) * nx + cx),
-                                        __ldg(src + (zo + clampi(yb - D_ + 2 * p + 1, ny)) * nx + cx));
+                ai[zz][p] = make_float2(ld(src + (zo + clampi(yb - D_ + 2 * p, ny)) * nx + cx),
+                                        ld(src + (zo + clampi(yb - D_ + 2 * p + 1, ny)) * nx + cx));
             }
     }
     float2 res[BZ];
@@ -370,16 +380,16 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ>::NT)
                 if (y < ny && z < nz) {
                     const long long o = i * nvox + ((long long)z * ny + y) * nx + x;
                     const float r = j == 0 ? res[k].x : res[k].y;
-                    float f = (mu * __ldg(g + o) + r) * inv;  // Eq. 8
-                    if (clip) f = fmaxf(f, 0.f);              // positivity (TNLM-R step 4)
-                    out[o] = f;
+                    float f = (mu * ld(g + o) + r) * inv;  // Eq. 8
+                    if (clip) f = fmaxf(f, 0.f);           // positivity (TNLM-R step 4)
+                    st(out + o, f);
                 }
             }
     }
 }
 
-template <int D_, int M_>
-bool launch_box(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g, float *out,
+template <int D_, int M_, class T>
+bool launch_box(int nx, int ny, int nz, int np, const T *wsrc, const T *vals, const T *g, T *out,
                 float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
 {
     constexpr int BY = 2, BZ = 4;
@@ -387,7 +397,7 @@ bool launch_box(int nx, int ny, int nz, int np, const float *wsrc, const float *
     const int ntx = (nx + C::TXO - 1) / C::TXO, nty = (ny + C::TY - 1) / C::TY, ntz = (nz + C::TZ - 1) / C::TZ;
     const long long blocks = (long long)ntx * nty * ntz * np;
     if (blocks > 0x7fffffffLL) return false;
-    auto kern = k_sweep_box<D_, M_, BY, BZ>;
+    auto kern = k_sweep_box<D_, M_, BY, BZ, T>;
     *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (*err != cudaSuccess) return true;
     kern<<<(unsigned)blocks, C::NT, C::SMEM, st>>>(nx, ny, nz, np, ntx, nty, ntz, wsrc, vals, g, out, c2, mu, clip);
@@ -524,6 +534,33 @@ tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, cons
         TNLM_TRY_CUDA(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sweep<<<grid, block, smem, st>>>(nx, ny, nz, np, ntz, wsrc, vals, g, out, d, M, c2, mu, clip);
     TNLM_TRY_CUDA(cudaGetLastError());
+    return TNLM_OK;
+}
+
+tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
+                              const uint16_t *g, uint16_t *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
+{
+    using B = __nv_bfloat16;
+    const B *W = reinterpret_cast<const B *>(wsrc), *V = reinterpret_cast<const B *>(vals);
+    const B *G = reinterpret_cast<const B *>(g);
+    B *O = reinterpret_cast<B *>(out);
+    const float c2 = exponent_scale(h);
+    cudaError_t err = cudaSuccess;
+    bool done = false;
+    if (d == 1 && M == 1) done = launch_box<1, 1>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    else if (d == 1 && M == 2) done = launch_box<1, 2>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    else if (d == 1 && M == 3) done = launch_box<1, 3>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 1) done = launch_box<2, 1>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 2) done = launch_box<2, 2>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    else if (d == 2 && M == 3) done = launch_box<2, 3>(nx, ny, nz, np, W, V, G, O, c2, mu, clip, st, &err);
+    if (!done) {
+        set_error("BF16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", d, M);
+        return TNLM_ERR_NOT_IMPLEMENTED;
+    }
+    if (err != cudaSuccess) {
+        set_error("BF16 sweep launch failed: %s", cudaGetErrorString(err));
+        return TNLM_ERR_CUDA;
+    }
     return TNLM_OK;
 }
 

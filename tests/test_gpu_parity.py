@@ -418,3 +418,39 @@ def test_fdk_matches_oracle(ora, name):
     ref = ora.fdk(OG, p)
     out = tnlm.tnlm_fdk(G, cuda(p)).cpu().numpy()
     assert rel_l2(out, ref) <= RTOL
+
+
+BF16_U = 2.0 ** -9  # unit roundoff of bfloat16 (8-bit significand, round to nearest)
+
+
+@pytest.mark.parametrize("shape,d,M", [((3, 9, 13, 19), 1, 3), ((3, 7, 10, 11), 2, 3), ((2, 8, 12, 20), 2, 1)])
+def test_bf16_sweep_is_rounded_fp32_sweep(ora, shape, d, M):
+    """BF16 storage / FP32 arithmetic: the sweep on BF16 images equals the
+    FP32 sweep on the same (BF16-valued) images rounded to BF16, bit for bit;
+    against the FP64 oracle its error is the output rounding (<= 2^-9)."""
+    a, v, g, h = _sweep_inputs(shape, 210, "smooth")
+    A, V, Gi = (torch.from_numpy(t).cuda().to(torch.bfloat16) for t in (a, v, g))
+    out_bf = tnlm.tnlm_gauss_jacobi_bf16(A, V, Gi, d, M, h, 0.8, 1)
+    out_f = tnlm.tnlm_gauss_jacobi(A.float().contiguous(), V.float().contiguous(), Gi.float().contiguous(), d, M, h,
+                                   0.8, 1)
+    assert torch.equal(out_bf, out_f.to(torch.bfloat16))
+    ref = ora.gj_sweep(A.float().cpu().numpy(), V.float().cpu().numpy(), Gi.float().cpu().numpy(), d, M, h, 0.8, 1)
+    assert rel_l2(out_bf.float().cpu().numpy(), ref) <= BF16_U
+
+
+def test_bf16_enhance_error_vs_fp64(ora):
+    """TNLM-E with BF16 storage over 5 sweeps against the FP64 oracle on the
+    same BF16-valued input: each sweep rounds its output (relative <= u) and
+    the Jacobi map contracts by 2/(2+mu), so the error stays below u/(1-2/3)."""
+    cfg = synth.EnhanceConfig("t", 4, (24, 20, 12), 1.0, 0.002, 0.003, 36, 2, 3, 0.04, 1.0, 5, 220)
+    g, _ = synth.enhance_input(cfg)
+    G = g.cuda().to(torch.bfloat16)
+    p = tnlm.Params(d=2, M=3, h=0.04, mu=1.0, n_outer=5, clip_nonneg=0)
+    f = tnlm.tnlm_enhance_bf16(G, p)
+    ref = ora.enhance(G.float().cpu().numpy(), 2, 3, 0.04, 1.0, 5)
+    err = rel_l2(f.float().cpu().numpy(), ref)
+    f32 = tnlm.tnlm_enhance(G.float().contiguous(), p).cpu().numpy()
+    err32 = rel_l2(f32, ref)
+    print(f"TNLM-E 5 sweeps vs FP64: BF16 storage rel-L2 {err:.3e}, FP32 {err32:.3e}")
+    assert err <= 3 * BF16_U
+    assert err32 <= RTOL
