@@ -396,6 +396,17 @@ def measure_variants(tnlm, synth, geom, y, stream) -> dict:
     out["tnlm_e_bf16_voxel_updates_per_s"] = round(nvox / (bf_ms / 1e3), 1)
     del g, f, gb, fb
     torch.cuda.empty_cache()
+    # differentiable total energy (frozen weights) on 10 x 128^3, 40 views x 256x192
+    c4 = synth.C4
+    pb4 = synth.recon_problem(c4, device="cuda")
+    g4 = tnlm.Geometry(pb4.geom)
+    f4 = (pb4.truth + 0.001).contiguous()
+    grad4 = torch.empty_like(f4)
+    p4 = tnlm.Params(d=c4.d, M=c4.M, h=c4.h, mu=c4.mu)
+    out["energy_grad_workload"] = "E(f) and grad E, 10 x 128^3 at 2 mm, 40 views x 256x192, patch 3^3, window 5^3"
+    out["energy_grad_ms"] = round(_time_ms(lambda: tnlm.tnlm_energy_grad(g4, pb4.y, f4, pb4.truth, p4, grad=grad4),
+                                           stream), 3)
+    g4.close()
     return out
 
 

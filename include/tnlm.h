@@ -197,6 +197,17 @@ tnlm_status tnlm_enhance_noalloc(int nx, int ny, int nz, int n_phases, const flo
  * allocates CGLS workspace in the handle (two volumes, one projection set). */
 tnlm_status tnlm_cgls(tnlm_geometry *geom, const float *y, float *x, int n_iter, double *report, void *stream);
 
+/* Total energy of Eq. 1 with the TNLM functional J of Eq. 2 evaluated over
+ * the search window with frozen weights (Eq. 9 from the weight-source images
+ * a, direction toward phase i+1, normalised over the window as in Eq. 8):
+ *   E(f) = mu/2 sum_i ||P_i f_i - y_i||^2 + 1/2 sum_i J[f_i, f_{i+1}],
+ * and its gradient with respect to f (for gradient-based training or
+ * reconstruction).  Uses params d, M, h, mu.  energy: HOST double; grad:
+ * [N_p][nz][ny][nx] device, overwritten; it must not overlap f or a.  The
+ * weights are recomputed, never stored.  Synchronises `stream`. */
+tnlm_status tnlm_energy_grad(tnlm_geometry *geom, const float *y, const float *f, const float *a,
+                             const tnlm_params *params, double *energy, float *grad, void *stream);
+
 /* FDK reconstruction (Feldkamp, Davis and Kress, the paper's ref. 16), the
  * initial value f^(0) of TNLM-R and the input g of TNLM-E (Sec. 2.2-2.3):
  * every phase from its own views, assumed to cover a full rotation evenly

@@ -82,6 +82,7 @@ def _load():
             "ora_reconstruct": (None, [G, _dp, _dp, d, i, i, d, d, i, i, i, i, i, i, C.c_void_p]),
             "ora_cgls": (None, [G, _dp, _dp, i, C.c_void_p]),
             "ora_fdk": (None, [G, _dp, _dp, C.c_void_p]),
+            "ora_energy_grad": (d, [G, _dp, _dp, _dp, i, i, d, d, _dp]),
             "ora_enhance": (None, [i, i, i, i, _dp, _dp, i, i, d, d, i, i]),
             "ora_num_threads": (i, []),
         }
@@ -208,6 +209,14 @@ def tnlm_energy(w, M: int, f) -> float:
     f = _f64(f)
     np_, nz, ny, nx = f.shape
     return _load().ora_tnlm_energy(nx, ny, nz, np_, _f64(w), M, f)
+
+
+def energy_grad(geom: Geometry, y, f, a, d: int, M: int, h: float, mu: float):
+    """(E, grad E) of Eq. 1 with J of Eq. 2 and frozen weights from a."""
+    grad = np.empty(geom.vol_shape, np.float64)
+    E = _load().ora_energy_grad(geom.ref, _f64(y).reshape(geom.proj_shape), _f64(f).reshape(geom.vol_shape),
+                                _f64(a).reshape(geom.vol_shape), d, M, h, mu, grad)
+    return E, grad
 
 
 def fidelity(geom: Geometry, f, y) -> float:

@@ -530,6 +530,57 @@ double ora_tnlm_energy(int nx, int ny, int nz, int np, const double *w, int M, c
     return J;
 }
 
+/* Total energy of Eq. 1 with the J of Eq. 2 over the search window and
+ * frozen weights (Eq. 9 from the weight-source images a, direction toward
+ * phase i+1, normalised over the window):
+ *   E(f) = mu/2 sum_i ||P_i f_i - y_i||^2 + 1/2 sum_i J[f_i, f_{i+1}],
+ * and its gradient, obtained by differentiating every term of the sums
+ * (scatter form): the pair (x in phase i, x+delta in phase i+1) adds
+ * w (f_i(x) - f_{i+1}(x+delta)) to grad_i(x) and subtracts it from
+ * grad_{i+1}(x+delta).  Returns E; grad has the volume layout. */
+double ora_energy_grad(const ora_geom *g, const double *yproj, const double *f, const double *a, int d, int M,
+                       double h, double mu, double *grad)
+{
+    const int np_ = g->np, nx = g->nx, ny = g->ny, nz = g->nz;
+    const long nvox = ora_nvox(g), nv = nvox * np_;
+    const long npr = (long)ora_total_views(g) * ora_npix(g);
+    const int S = 2 * M + 1, W = S * S * S;
+    double *r = (double *)malloc(sizeof(double) * npr);
+    ora_project(g, f, r);
+    double fid = 0.0;
+    for (long t = 0; t < npr; ++t) {
+        r[t] -= yproj[t];
+        fid += r[t] * r[t];
+    }
+    ora_backproject(g, r, grad);
+    for (long t = 0; t < nv; ++t) grad[t] *= mu;
+    double *w = (double *)malloc(sizeof(double) * nv * 2 * W);
+    ora_weights(nx, ny, nz, np_, a, d, M, h, w);
+    double J = 0.0;
+    for (int i = 0; i < np_; ++i) {
+        const int j = (i + 1) % np_;
+        for (long v = 0; v < nvox; ++v) {
+            const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
+            const double *wv = w + (((long)i * 2 + 0) * nvox + v) * W;
+            int k = 0;
+            for (int dz = -M; dz <= M; ++dz)
+                for (int dy = -M; dy <= M; ++dy)
+                    for (int dx = -M; dx <= M; ++dx, ++k) {
+                        const int X = x + dx, Y = y + dy, Z = z + dz;
+                        if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz) continue;
+                        const long q = ((long)Z * ny + Y) * nx + X;
+                        const double diff = f[(long)i * nvox + v] - f[(long)j * nvox + q];
+                        J += wv[k] * diff * diff;
+                        grad[(long)i * nvox + v] += wv[k] * diff;
+                        grad[(long)j * nvox + q] -= wv[k] * diff;
+                    }
+        }
+    }
+    free(r);
+    free(w);
+    return 0.5 * mu * fid + 0.5 * J;
+}
+
 /* sum_i ||P_i f_i - y_i||^2 */
 double ora_fidelity(const ora_geom *g, const double *f, const double *yproj)
 {

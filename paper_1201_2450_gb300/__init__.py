@@ -28,6 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
+    "tnlm_energy_grad", "TNLMEnergy",
     "reconstruct_host", "library_path",
 ]
 
@@ -114,6 +115,7 @@ def _load():
             "tnlm_cgls": (i, [vp, vp, vp, i, vp, vp]),
             "tnlm_fdk": (i, [vp, vp, vp, vp]),
             "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_energy_grad": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -335,6 +337,38 @@ def tnlm_enhance_bf16(g: torch.Tensor, params: Params, out: torch.Tensor | None 
     _check(_load().tnlm_enhance_bf16(nx, ny, nz, np_, _dev(g, "g", dtype=bf), _dev(out, "f", g.device, g.shape, bf),
                                      C.byref(p), _stream(stream)), "tnlm_enhance_bf16")
     return out
+
+
+def tnlm_energy_grad(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: torch.Tensor, params: Params,
+                     grad: torch.Tensor | None = None, stream=None):
+    """(E, grad E) of Eq. 1 with J of Eq. 2 and frozen Eq. 9 weights from a."""
+    if grad is None:
+        grad = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+    E = C.c_double()
+    p = params._c()
+    _check(_load().tnlm_energy_grad(geom.handle, _dev(y, "y", geom.device, geom.proj_shape),
+                                    _dev(f, "f", geom.device, geom.vol_shape), _dev(a, "a", geom.device, geom.vol_shape),
+                                    C.byref(p), C.byref(E), _dev(grad, "grad", geom.device, geom.vol_shape),
+                                    _stream(stream)), "tnlm_energy_grad")
+    return E.value, grad
+
+
+class TNLMEnergy(torch.autograd.Function):
+    """E(f) of Eq. 1 (J of Eq. 2, weights frozen from a) as an autograd
+    function: the forward pass computes the energy and its gradient with the
+    library's kernels (projector, transpose, TNLM adjoint); the backward pass
+    scales that gradient.  Usage: E = TNLMEnergy.apply(f, geom, y, a, params)."""
+
+    @staticmethod
+    def forward(ctx, f, geom, y, a, params):
+        E, grad = tnlm_energy_grad(geom, y, f.detach().contiguous(), a.detach().contiguous(), params)
+        ctx.save_for_backward(grad)
+        return torch.tensor(E, dtype=torch.float64, device=f.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        (grad,) = ctx.saved_tensors
+        return (gE.to(grad.dtype) * grad, None, None, None, None)
 
 
 def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:

@@ -302,6 +302,7 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_pseg);
     cudaFree(g->d_cscal);
     cudaFree(g->d_cpart);
+    cudaFree(g->d_epart);
     delete g;
 }
 
@@ -535,6 +536,33 @@ tnlm_status tnlm_cgls(tnlm_geometry *geo, const float *y, float *x, int n_iter, 
         TNLM_TRY_CUDA(cudaMemcpyAsync(report, geo->d_scalars, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
         TNLM_TRY_CUDA(cudaStreamSynchronize(st));
     }
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_energy_grad(tnlm_geometry *geo, const float *y, const float *f, const float *a,
+                             const tnlm_params *p, double *energy, float *grad, void *stream)
+{
+    if (!geo || !y || !f || !a || !p || !energy || !grad)
+        return arg_error("geometry, y, f, a, params, energy and grad must not be NULL");
+    const KGeom &kg = geo->kg;
+    TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
+    if (grad == f || grad == a) return arg_error("grad must not alias f or a");
+    TNLM_TRY(ensure_workspace(geo, true, 4));
+    const long long nblk = energy_blocks(kg.nx, kg.ny, kg.nz, kg.np);
+    if (!geo->d_epart) TNLM_TRY(dev_alloc(&geo->d_epart, (size_t)nblk));
+    cudaStream_t st = as_stream(stream);
+    // fidelity: r|D| and ||P f - y||^2; grad = mu P^T (P f - y)
+    TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, f, y, geo->d_r, geo->d_part, 1, st));
+    TNLM_TRY(launch_sum_partials(geo->d_part, forward_blocks(kg, geo->n_views_total), geo->d_scalars, st));
+    TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, grad, grad, p->mu, 0.0f, true,
+                                prefix_workspace(geo), geo->n_views_total, st));
+    // TNLM part with frozen weights from a
+    TNLM_TRY(launch_energy_tnlm(kg.nx, kg.ny, kg.nz, kg.np, a, f, p->d, p->M, p->h, geo->d_tmp, grad, geo->d_epart, st));
+    TNLM_TRY(launch_sum_partials(geo->d_epart, nblk, geo->d_scalars + 1, st));
+    double sc[2];
+    TNLM_TRY_CUDA(cudaMemcpyAsync(sc, geo->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+    *energy = 0.5 * (double)p->mu * sc[0] + 0.5 * sc[1];
     return TNLM_OK;
 }
 

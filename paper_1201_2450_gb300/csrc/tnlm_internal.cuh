@@ -105,6 +105,12 @@ struct CglsArgs {
 };
 tnlm_status run_cgls(const CglsArgs &a, cudaStream_t st);
 
+// TNLM part of the energy gradient (energy.cu): lam (np*nvox scratch) <- log-normalisers,
+// grad += TNLM gradient, jpart[energy_blocks()] <- FP64 partials of J.
+tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, const float *f, int d, int M, float h,
+                               float *lam, float *grad, double *jpart, cudaStream_t st);
+long long energy_blocks(int nx, int ny, int nz, int np);
+
 // FDK of every phase from its own views (fdk.cu); filt: projection-sized scratch.
 tnlm_status launch_fdk(const KGeom &kg, const ViewGeom *views, const int *view_off, int n_views_total,
                        const float *proj, float *filt, float *vol, cudaStream_t st);
@@ -140,6 +146,7 @@ struct tnlm_geometry {
     long long *d_pseg = nullptr;      // [np+1]
     double *d_cscal = nullptr;        // 3 * np
     double *d_cpart = nullptr;        // CGLS reduction partials
+    double *d_epart = nullptr;        // energy reduction partials
     long long scalars_len = 0;
     // instrumentation
     int timing = 0;

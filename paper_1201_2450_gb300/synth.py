@@ -117,6 +117,9 @@ C1 = ReconConfig("plain TNLM-R FP32 4x32^3, 20 views x 64x48", 4, (32, 32, 32), 
 # 10 phases, 256x256x64 at 2 mm, 36 views/phase on 512x384 at 0.78 mm, patch 3^3, window 7^3, 50 iterations
 C2 = ReconConfig("NCAT-shaped TNLM-R FP32 10x256x256x64, 36 views x 512x384", 10, (256, 256, 64), 2.0, 36,
                  (512, 384), 0.78, 5e4, 1, 3, 0.02, 1.0, 50, "thorax", 1002)
+# differentiable-energy workload: 10 phases, 128^3 at 2 mm, 40 views/phase on 256x192 at 1.56 mm
+C4 = ReconConfig("differentiable energy 10x128^3, 40 views x 256x192", 10, (128, 128, 128), 2.0, 40, (256, 192),
+                 1.56, 5e4, 1, 2, 0.02, 1.0, 1, "thorax", 1004)
 # reduced C2 with the same structure, for full-length parity runs
 C2_SMALL = ReconConfig("NCAT-shaped TNLM-R reduced 10x64x64x16, 9 views x 128x96", 10, (64, 64, 16), 8.0, 9,
                        (128, 96), 3.12, 5e4, 1, 3, 0.02, 1.0, 50, "thorax", 1002)

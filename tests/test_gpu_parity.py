@@ -454,3 +454,66 @@ def test_bf16_enhance_error_vs_fp64(ora):
     print(f"TNLM-E 5 sweeps vs FP64: BF16 storage rel-L2 {err:.3e}, FP32 {err32:.3e}")
     assert err <= 3 * BF16_U
     assert err32 <= RTOL
+
+
+def _energy_inputs(shape, proj_shape, seed):
+    """Well-conditioned inputs for the gradient checks: f and y independent of
+    the weight source, so the residual P f - y and the TNLM terms are O(1)
+    (with f ~ a and y ~ P a both are small differences of large numbers and
+    FP32 loses ~log10(|P f| / |P f - y|) digits -- a property of the data,
+    not of the kernels)."""
+    a = synth.smooth_volume(shape, seed)
+    f = synth.uniform(shape, seed + 1, 0.0, 0.04)
+    y = synth.uniform(proj_shape, seed + 2, 0.0, 0.3)
+    return a, f, y
+
+
+@pytest.mark.parametrize("name", ["ragged_uneven", "c1"])
+def test_energy_grad_matches_oracle(ora, name):
+    """E(f) of Eq. 1 (J of Eq. 2, frozen Eq. 9 weights from a) and its
+    gradient against the FP64 oracle's scatter-form gradient."""
+    geom = GEOMS[name]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    a, f, y = _energy_inputs(G.vol_shape, G.proj_shape, 230)
+    p = tnlm.Params(d=1, M=2, h=0.02, mu=0.7)
+    E_ref, g_ref = ora.energy_grad(OG, y, f, a, 1, 2, 0.02, 0.7)
+    E, g = tnlm.tnlm_energy_grad(G, cuda(y), cuda(f), cuda(a), p)
+    assert E == pytest.approx(E_ref, rel=1e-5)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= RTOL
+
+
+def test_energy_grad_two_phases(ora):
+    geom = synth.make_geometry(nx=14, ny=12, nz=9, dx=1.0, nu=30, nv=14, du=1.2, sad=200, sdd=300, n_phases=2,
+                               views_per_phase=[5, 6], angle_offset=0.1)
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    a, f, y = _energy_inputs(G.vol_shape, G.proj_shape, 233)
+    E_ref, g_ref = ora.energy_grad(OG, y, f, a, 2, 1, 0.03, 1.3)
+    E, g = tnlm.tnlm_energy_grad(G, cuda(y), cuda(f), cuda(a), tnlm.Params(d=2, M=1, h=0.03, mu=1.3))
+    assert E == pytest.approx(E_ref, rel=1e-5)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= RTOL
+
+
+def test_energy_autograd_and_directional_derivatives(ora):
+    """TNLMEnergy in autograd: f.grad is the kernels' gradient, and along 64
+    random directions it matches FP64 central differences of the oracle's
+    energy."""
+    geom = GEOMS["c1"]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    a, f0, y = _energy_inputs(G.vol_shape, G.proj_shape, 235)
+    p = tnlm.Params(d=1, M=2, h=0.02, mu=0.7)
+    f = cuda(f0).requires_grad_(True)
+    E = tnlm.TNLMEnergy.apply(f, G, cuda(y), cuda(a), p)
+    (2.0 * E).backward()
+    _, g = tnlm.tnlm_energy_grad(G, cuda(y), cuda(f0), cuda(a), p)
+    assert torch.allclose(f.grad, 2.0 * g)
+    gh = g.double().cpu().numpy()
+    rng = np.random.default_rng(237)
+    eps = 1e-4
+    for _ in range(64):
+        v = rng.standard_normal(G.vol_shape)
+        fd = (ora.energy_grad(OG, y, f0 + eps * v, a, 1, 2, 0.02, 0.7)[0] -
+              ora.energy_grad(OG, y, f0 - eps * v, a, 1, 2, 0.02, 0.7)[0]) / (2 * eps)
+        assert float((gh * v).sum()) == pytest.approx(fd, rel=1e-4)

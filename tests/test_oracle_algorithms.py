@@ -156,3 +156,24 @@ def test_fdk_reconstructs_known_balls(ora):
         out = d2 > (r + 4.0) ** 2
         assert abs(f[ph][core].mean() - m) < 0.005 * m, (ph, f[ph][core].mean())
         assert abs(f[ph][out].mean()) < 0.01 * m
+
+
+def test_energy_gradient_finite_differences(ora):
+    """The oracle's total energy (Eq. 1, J of Eq. 2, frozen Eq. 9 weights)
+    equals its parts, and its gradient matches FP64 central differences along
+    64 random directions."""
+    geom, truth, y = _small_problem(70)
+    G = ora.Geometry(geom)
+    f = truth.astype(np.float64) + synth.normal(G.vol_shape, 71, 0.002)
+    a = truth.astype(np.float64)
+    d, M, h, mu = 1, 1, 0.02, 0.7
+    E, grad = ora.energy_grad(G, y, f, a, d, M, h, mu)
+    w = ora.weights(a, d, M, h)
+    assert E == pytest.approx(0.5 * mu * ora.fidelity(G, f, y) + 0.5 * ora.tnlm_energy(w, M, f), rel=1e-12)
+    rng = np.random.default_rng(72)
+    eps = 1e-4
+    for _ in range(64):
+        v = rng.standard_normal(G.vol_shape)
+        fd = (ora.energy_grad(G, y, f + eps * v, a, d, M, h, mu)[0] -
+              ora.energy_grad(G, y, f - eps * v, a, d, M, h, mu)[0]) / (2 * eps)
+        assert fd == pytest.approx(float((grad * v).sum()), rel=1e-7, abs=1e-12)
