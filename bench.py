@@ -407,7 +407,61 @@ def measure_variants(tnlm, synth, geom, y, stream) -> dict:
     out["energy_grad_ms"] = round(_time_ms(lambda: tnlm.tnlm_energy_grad(g4, pb4.y, f4, pb4.truth, p4, grad=grad4),
                                            stream), 3)
     g4.close()
+    del pb4, f4, grad4
+    torch.cuda.empty_cache()
+    out.update(measure_batch(tnlm, synth, stream))
     return out
+
+
+def batch_configs(n: int = 16, seed: int = 1005):
+    """Uneven TNLM-R problems: 6-10 phases, volumes from 128x128x48 to
+    256x256x96 (same 512 x 512 x 192 mm field), 20-60 views per phase (uneven
+    within a problem), 384x288 or 512x384 detectors of the same 399 x 300 mm
+    area; patch 3^3, window 7^3."""
+    from paper_1201_2450_gb300 import synth
+    rng = np.random.default_rng(seed)
+    cfgs = []
+    for b in range(n):
+        nph = int(rng.integers(6, 11))
+        k = int(rng.integers(0, 5))  # 0..4 -> 128..256 in steps of 32
+        nx, nz = 128 + 32 * k, 48 + 12 * k
+        nu, nv = (384, 288) if rng.uniform() < 0.5 else (512, 384)
+        views = [int(v) for v in rng.integers(20, 61, size=nph)]
+        cfgs.append(synth.ReconConfig(f"batch problem {b}", nph, (nx, nx, nz), 512.0 / nx, views, (nu, nv),
+                                      399.4 / nu, 5e4, 1, 3, 0.02, 1.0, 3, "thorax", 2000 + b))
+    return cfgs
+
+
+def measure_batch(tnlm, synth, stream, n_outer: int = 3) -> dict:
+    cfgs = batch_configs()
+    probs = [synth.recon_problem(c, device="cuda") for c in cfgs]
+    geoms = [tnlm.Geometry(pb.geom) for pb in probs]
+    ys = [pb.y.contiguous() for pb in probs]
+    params = [tnlm.Params(d=c.d, M=c.M, h=c.h, mu=c.mu, tau=2e-6, n_outer=n_outer) for c in cfgs]
+    fs = [torch.zeros(g.vol_shape, device="cuda") for g in geoms]
+
+    def seq():
+        for g, y, f, p in zip(geoms, ys, fs, params):
+            tnlm.tnlm_reconstruct(g, y, f, p)
+
+    def batch():
+        tnlm.tnlm_reconstruct_batch(geoms, ys, fs, params)
+
+    seq_ms = _time_ms(seq, stream, reps=1)
+    bat_ms = _time_ms(batch, stream, reps=1)
+    n_it = n_outer * len(cfgs)
+    voxels = sum(c.n_phases * c.vol[0] * c.vol[1] * c.vol[2] for c in cfgs)
+    res = {"batch16_workload": "16 uneven TNLM-R problems (6-10 phases, 128^2x48..256^2x96, 20-60 views/phase, "
+                               "384x288 or 512x384), 3 FBS iterations each, FP32",
+           "batch16_total_voxels": voxels,
+           "batch16_graph_ms": round(bat_ms, 2), "batch16_sequential_ms": round(seq_ms, 2),
+           "batch16_graph_problem_iterations_per_s": round(n_it / (bat_ms / 1e3), 3),
+           "batch16_sequential_problem_iterations_per_s": round(n_it / (seq_ms / 1e3), 3)}
+    for g in geoms:
+        g.close()
+    del probs, ys, fs
+    torch.cuda.empty_cache()
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -145,6 +145,16 @@ tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float 
 tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, const tnlm_params *params,
                              double *report, void *stream);
 
+/* TNLM-R for a batch of independent problems (uneven sizes, phase counts
+ * and view counts allowed) in one CUDA graph: one FBS iteration of every
+ * problem is captured (problems on parallel graph branches) and the graph
+ * is replayed n_outer times on `stream`, after the work already queued
+ * there.  geoms[b], y[b], f[b], params[b] as for tnlm_reconstruct (no
+ * report, no stage timing); every params[b].n_outer must be equal; a handle
+ * may appear once.  Workspaces are allocated before the capture. */
+tnlm_status tnlm_reconstruct_batch(int n_problems, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                   const tnlm_params *params, void *stream);
+
 /* TNLM-E (Sec. 2.3): f^(0) = g, then params->n_outer sweeps of (weights of
  * Eq. 9 from f^(k), Eq. 8 with fidelity image g).  Uses params d, M, h, mu,
  * n_outer and clip_nonneg.  g and f must not overlap.  Allocates one

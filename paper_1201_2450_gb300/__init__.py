@@ -28,7 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
-    "tnlm_energy_grad", "TNLMEnergy",
+    "tnlm_energy_grad", "TNLMEnergy", "tnlm_reconstruct_batch",
     "reconstruct_host", "library_path",
 ]
 
@@ -116,6 +116,7 @@ def _load():
             "tnlm_fdk": (i, [vp, vp, vp, vp]),
             "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_energy_grad": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
+            "tnlm_reconstruct_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params), vp]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -271,6 +272,20 @@ def tnlm_reconstruct(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: P
                                     rep.ctypes.data if rep is not None else None, _stream(stream)),
            "tnlm_reconstruct")
     return f, rep
+
+
+def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
+    """TNLM-R on independent problems in one graph replayed n_outer times;
+    every f is updated in place."""
+    n = len(geoms)
+    if not (len(ys) == len(fs) == len(params) == n):
+        raise ValueError("geoms, ys, fs and params must have the same length")
+    G = (C.c_void_p * n)(*[g.handle.value for g in geoms])
+    Y = (C.c_void_p * n)(*[_dev(y, "y", g.device, g.proj_shape) for g, y in zip(geoms, ys)])
+    F = (C.c_void_p * n)(*[_dev(f, "f", g.device, g.vol_shape) for g, f in zip(geoms, fs)])
+    P = (_Params * n)(*[p._c() for p in params])
+    _check(_load().tnlm_reconstruct_batch(n, G, Y, F, P, _stream(stream)), "tnlm_reconstruct_batch")
+    return fs
 
 
 def tnlm_enhance(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -361,58 +361,84 @@ static tnlm_status check_params(const tnlm_params *p, bool recon)
     return TNLM_OK;
 }
 
-tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, double *report,
-                             void *stream)
+}  // extern "C"
+
+namespace tnlm {
+
+// Validate one TNLM-R problem and allocate everything its iterations use, so
+// that an iteration issues only stream-ordered work (capturable).
+static tnlm_status prepare_reconstruct(tnlm_geometry *geo, const float *y, const float *f, const tnlm_params *p,
+                                       long long n_slots)
 {
     if (!geo || !y || !f) return arg_error("geometry, y and f must not be NULL");
     TNLM_TRY(check_params(p, true));
     const KGeom &kg = geo->kg;
     TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
-    const long long n_norms = (long long)p->n_outer * p->n_inner;
-    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
     TNLM_TRY(ensure_workspace(geo, p->gj_start == 1 || p->n_gj > 1, n_slots > 1 ? n_slots : 1));
     if (p->p1_solver == 1) TNLM_TRY(ensure_cgls_workspace(geo));
+    prefix_workspace(geo);
+    return TNLM_OK;
+}
+
+// One FBS iteration k of TNLM-R (Sec. 2.3) on stream st; timer may be null.
+static tnlm_status fbs_iteration(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, int k,
+                                 bool report, StageTimer *timer, cudaStream_t st)
+{
+    const KGeom &kg = geo->kg;
+    const long long nblk = forward_blocks(kg, geo->n_views_total);
+    // step 1: (P1) from f^(k-1): CGLS (the paper's solver) or n_inner gradient steps
+    if (p->p1_solver == 1) {
+        if (timer) timer->begin(0);
+        TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+        TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
+                                    report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
+                          st));
+        if (timer) timer->end();
+    }
+    for (int t = 0; t < (p->p1_solver == 1 ? 0 : p->n_inner); ++t) {
+        const float *src = t == 0 ? f : geo->d_g;
+        if (timer) timer->begin(0);
+        TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
+        if (timer) timer->end();
+        if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
+        if (timer) timer->begin(1);
+        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, geo->d_g, -p->tau, 1.0f, true,
+                                    prefix_workspace(geo), geo->n_views_total, st));
+        if (timer) timer->end();
+    }
+    // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
+    if (timer) timer->begin(2);
+    const int ngj = p->n_gj > 0 ? p->n_gj : 1;
+    const float *vals = p->gj_start ? f : geo->d_g;
+    for (int l = 0; l < ngj; ++l) {
+        // sweeps alternate between f and the scratch image so that the last lands in f; with
+        // gj_start = 1 the first sweep reads f and must write the scratch image
+        float *dst = ((ngj - 1 - l) % 2 == 0) ? f : geo->d_tmp;
+        if (dst == vals) dst = (vals == f) ? geo->d_tmp : f;  // never read and write one image
+        TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, vals, geo->d_g, dst, p->d, p->M, p->h, p->mu,
+                              p->clip_nonneg && l == ngj - 1, st));
+        vals = dst;
+    }
+    if (vals != f)
+        TNLM_TRY_CUDA(cudaMemcpyAsync(f, vals, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+    if (timer) timer->end();
+    return TNLM_OK;
+}
+
+}  // namespace tnlm
+
+extern "C" {
+
+tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, double *report,
+                             void *stream)
+{
+    if (!p) return arg_error("params must not be NULL");
+    const long long n_norms = (long long)p->n_outer * p->n_inner;
+    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
+    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots));
     cudaStream_t st = as_stream(stream);
     StageTimer timer(geo, st);
-    const long long nblk = forward_blocks(kg, geo->n_views_total);
-    for (int k = 0; k < p->n_outer; ++k) {
-        // step 1: (P1) from f^(k-1): CGLS (the paper's solver) or n_inner gradient steps
-        if (p->p1_solver == 1) {
-            timer.begin(0);
-            TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
-            TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
-                                        report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
-                              st));
-            timer.end();
-        }
-        for (int t = 0; t < (p->p1_solver == 1 ? 0 : p->n_inner); ++t) {
-            const float *src = t == 0 ? f : geo->d_g;
-            timer.begin(0);
-            TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
-            timer.end();
-            if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
-            timer.begin(1);
-            TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, geo->d_g, -p->tau, 1.0f,
-                                        true, prefix_workspace(geo), geo->n_views_total, st));
-            timer.end();
-        }
-        // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
-        timer.begin(2);
-        const int ngj = p->n_gj > 0 ? p->n_gj : 1;
-        const float *vals = p->gj_start ? f : geo->d_g;
-        for (int l = 0; l < ngj; ++l) {
-            // sweeps alternate between f and the scratch image so that the last lands in f; with
-            // gj_start = 1 the first sweep reads f and must write the scratch image
-            float *dst = ((ngj - 1 - l) % 2 == 0) ? f : geo->d_tmp;
-            if (dst == vals) dst = (vals == f) ? geo->d_tmp : f;  // never read and write one image
-            TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, vals, geo->d_g, dst, p->d, p->M, p->h,
-                                  p->mu, p->clip_nonneg && l == ngj - 1, st));
-            vals = dst;
-        }
-        if (vals != f)
-            TNLM_TRY_CUDA(cudaMemcpyAsync(f, vals, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
-        timer.end();
-    }
+    for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration(geo, y, f, p, k, report != nullptr, &timer, st));
     if (report && n_norms > 0) {
         if (p->p1_solver == 1) {  // keep the residual before each of the n_inner CGLS iterations
             std::vector<double> tmp((size_t)n_slots);
@@ -426,6 +452,71 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
         }
     }
     return timer.finish();
+}
+
+tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                   const tnlm_params *params, void *stream)
+{
+    if (n < 1 || !geoms || !y || !f || !params) return arg_error("need n >= 1 and non-NULL arrays");
+    const int n_outer = params[0].n_outer;
+    for (int b = 0; b < n; ++b) {
+        if (params[b].n_outer != n_outer) return arg_error("all problems of a batch need the same n_outer");
+        for (int c = 0; c < b; ++c)
+            if (geoms[c] == geoms[b]) return arg_error("a geometry handle may appear once per batch (it owns the workspace)");
+        TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1));
+    }
+    if (n_outer == 0) return TNLM_OK;
+    cudaStream_t st = as_stream(stream);
+    const int ns = n < 8 ? n : 8;  // parallel branches of the graph
+    cudaStream_t cs = nullptr;
+    std::vector<cudaStream_t> side(ns, nullptr);
+    std::vector<cudaEvent_t> join(ns, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    tnlm_status status = TNLM_OK;
+    auto cuda_ok = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && status == TNLM_OK) {
+            set_error("%s failed: %s", what, cudaGetErrorString(e));
+            status = TNLM_ERR_CUDA;
+        }
+        return status == TNLM_OK;
+    };
+    if (cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate") &&
+        cuda_ok(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "cudaEventCreate")) {
+        for (int s = 0; s < ns && status == TNLM_OK; ++s) {
+            cuda_ok(cudaStreamCreateWithFlags(&side[s], cudaStreamNonBlocking), "cudaStreamCreate");
+            cuda_ok(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    // capture one iteration of every problem: fork to the side streams, join back
+    if (status == TNLM_OK && cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture")) {
+        cuda_ok(cudaEventRecord(fork, cs), "cudaEventRecord");
+        for (int s = 0; s < ns; ++s) cuda_ok(cudaStreamWaitEvent(side[s], fork, 0), "cudaStreamWaitEvent");
+        for (int b = 0; b < n && status == TNLM_OK; ++b) {
+            tnlm_status sb = fbs_iteration(geoms[b], y[b], f[b], &params[b], 0, false, nullptr, side[b % ns]);
+            if (sb != TNLM_OK) status = sb;
+        }
+        for (int s = 0; s < ns; ++s) {
+            cudaEventRecord(join[s], side[s]);
+            cudaStreamWaitEvent(cs, join[s], 0);
+        }
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cuda_ok(e, "cudaStreamEndCapture");
+    }
+    if (status == TNLM_OK && cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate")) {
+        // replays on the caller's stream, after the work already queued there
+        for (int k = 0; k < n_outer && status == TNLM_OK; ++k) cuda_ok(cudaGraphLaunch(exec, st), "cudaGraphLaunch");
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int s = 0; s < ns; ++s) {
+        if (join[s]) cudaEventDestroy(join[s]);
+        if (side[s]) cudaStreamDestroy(side[s]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cs) cudaStreamDestroy(cs);
+    return status;
 }
 
 tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *f, const tnlm_params *p, void *stream)

@@ -517,3 +517,28 @@ def test_energy_autograd_and_directional_derivatives(ora):
         fd = (ora.energy_grad(OG, y, f0 + eps * v, a, 1, 2, 0.02, 0.7)[0] -
               ora.energy_grad(OG, y, f0 - eps * v, a, 1, 2, 0.02, 0.7)[0]) / (2 * eps)
         assert float((gh * v).sum()) == pytest.approx(fd, rel=1e-4)
+
+
+def test_reconstruct_batch_graph_equals_single_calls():
+    """Uneven problems in one captured graph replayed n_outer times give the
+    same images, bit for bit, as separate tnlm_reconstruct calls."""
+    geoms = [GEOMS["ragged_uneven"], synth.C1.geometry(),
+             synth.make_geometry(nx=20, ny=18, nz=10, dx=1.5, nu=40, nv=24, du=1.2, sad=300, sdd=450, n_phases=5,
+                                 views_per_phase=[6, 7, 5, 8, 6], angle_offset=0.07)]
+    params = [tnlm.Params(d=1, M=2, h=0.02, mu=0.8, tau=1e-4, n_outer=3),
+              tnlm.Params(d=1, M=2, h=0.02, mu=1.0, n_outer=3, n_inner=2, p1_solver=1),
+              tnlm.Params(d=2, M=1, h=0.03, mu=1.2, tau=5e-5, n_outer=3, n_gj=2)]
+    Gs = [tnlm.Geometry(g) for g in geoms]
+    ys = [cuda(synth.uniform(G.proj_shape, 240 + k) * 0.3) for k, G in enumerate(Gs)]
+    f0 = [synth.smooth_volume(G.vol_shape, 250 + k) for k, G in enumerate(Gs)]
+    single = []
+    for G, y, f, p in zip(Gs, ys, f0, params):
+        x = cuda(f)
+        tnlm.tnlm_reconstruct(G, y, x, p)
+        single.append(x)
+    Gb = [tnlm.Geometry(g) for g in geoms]
+    fb = [cuda(f) for f in f0]
+    tnlm.tnlm_reconstruct_batch(Gb, ys, fb, params)
+    torch.cuda.synchronize()
+    for a, b in zip(single, fb):
+        assert torch.equal(a, b)
