@@ -46,10 +46,12 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # each kernel on this workload, with the SHA-256 of the kernel source it was
 # measured on; a changed source invalidates the figure (reported as null).
 NCU_TRAFFIC = {
-    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload
-    "k_forward": {"bytes_per_launch": int((270.937344e6 + 148.07168e6) * 10 / 6), "source_sha": "08659ac9224f4ad0"},
-    "k_backproject": {"bytes_per_launch": int((257.549056e6 + 84.06528e6) * 10 / 6), "source_sha": "08659ac9224f4ad0"},
-    "k_sweep": {"bytes_per_launch": int((162.815232e6 + 84.133888e6) * 10 / 6), "source_sha": "804f2d99419ea900"},
+    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
+    # the transpose stage is the column scan plus the band kernel
+    "k_forward": {"bytes_per_launch": int((271.968256e6 + 148.052992e6) * 10 / 6), "source_sha": "983c825a053aa4ca"},
+    "k_backproject": {"bytes_per_launch": int((169.98144e6 + 285.81632e6 + 556.105728e6 + 92.62976e6) * 10 / 6),
+                      "source_sha": "983c825a053aa4ca"},
+    "k_sweep": {"bytes_per_launch": int((162.723328e6 + 84.157952e6) * 10 / 6), "source_sha": "551f684abbbc1a01"},
 }
 
 
@@ -410,7 +412,28 @@ def measure_variants(tnlm, synth, geom, y, stream) -> dict:
     del pb4, f4, grad4
     torch.cuda.empty_cache()
     out.update(measure_batch(tnlm, synth, stream))
+    out.update(measure_c1_latency(tnlm, synth, stream))
     return out
+
+
+def measure_c1_latency(tnlm, synth, stream) -> dict:
+    """The small plain TNLM-R problem (4 x 32^3, 20 views x 64x48, patch 3^3,
+    window 5^3, 5 iterations) is launch-bound: ms per FBS iteration through
+    tnlm_reconstruct (one launch sequence per iteration) and through the
+    captured-graph form (tnlm_reconstruct_batch with one problem)."""
+    c1 = synth.C1
+    pb = synth.recon_problem(c1, device="cuda")
+    g = tnlm.Geometry(pb.geom)
+    p = tnlm.Params(d=c1.d, M=c1.M, h=c1.h, mu=c1.mu, tau=1e-4, n_outer=c1.n_outer)
+    f = torch.zeros(g.vol_shape, device="cuda")
+    plain = _time_ms(lambda: tnlm.tnlm_reconstruct(g, pb.y, f, p), stream, reps=5)
+    plan = tnlm.BatchPlan([g], [pb.y], [f], [p])
+    graph = _time_ms(lambda: plan.run(c1.n_outer), stream, reps=5)
+    plan.close()
+    g.close()
+    return {"c1_workload": "plain TNLM-R FP32 4 x 32^3, 20 views x 64x48, patch 3^3, window 5^3, 5 iterations",
+            "c1_ms_per_iteration": round(plain / c1.n_outer, 4),
+            "c1_graph_ms_per_iteration": round(graph / c1.n_outer, 4)}
 
 
 def batch_configs(n: int = 16, seed: int = 1005):

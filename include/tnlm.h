@@ -155,6 +155,22 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, cons
 tnlm_status tnlm_reconstruct_batch(int n_problems, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
                                    const tnlm_params *params, void *stream);
 
+/* The same batch as a reusable plan: tnlm_batch_plan_create validates the
+ * problems, allocates their workspaces and captures one FBS iteration of
+ * all of them into an instantiated CUDA graph (params[b].n_outer is not
+ * used and may differ); tnlm_batch_plan_run replays it n_iterations times
+ * on `stream`, continuing from the current contents of every f[b].  The plan
+ * binds the handles and the y / f pointers given at creation: they must
+ * stay valid, and the handles unused by other calls, while replays are
+ * queued.  tnlm_reconstruct_batch(n, ...) equals create + run(n_outer) +
+ * destroy.  Destroying a plan whose replays are still queued is allowed
+ * (the graph is released when they finish). */
+typedef struct tnlm_batch_plan tnlm_batch_plan;
+tnlm_status tnlm_batch_plan_create(int n_problems, tnlm_geometry *const *geoms, const float *const *y,
+                                   float *const *f, const tnlm_params *params, tnlm_batch_plan **out);
+tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream);
+void tnlm_batch_plan_destroy(tnlm_batch_plan *plan);
+
 /* TNLM-E (Sec. 2.3): f^(0) = g, then params->n_outer sweeps of (weights of
  * Eq. 9 from f^(k), Eq. 8 with fidelity image g).  Uses params d, M, h, mu,
  * n_outer and clip_nonneg.  g and f must not overlap.  Allocates one

@@ -28,7 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
-    "tnlm_energy_grad", "TNLMEnergy", "tnlm_reconstruct_batch",
+    "tnlm_energy_grad", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan",
     "reconstruct_host", "library_path",
 ]
 
@@ -117,6 +117,10 @@ def _load():
             "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_energy_grad": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
             "tnlm_reconstruct_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params), vp]),
+            "tnlm_batch_plan_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
+                                           C.POINTER(vp)]),
+            "tnlm_batch_plan_run": (i, [vp, i, vp]),
+            "tnlm_batch_plan_destroy": (None, [vp]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -274,9 +278,7 @@ def tnlm_reconstruct(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: P
     return f, rep
 
 
-def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
-    """TNLM-R on independent problems in one graph replayed n_outer times;
-    every f is updated in place."""
+def _batch_args(geoms, ys, fs, params):
     n = len(geoms)
     if not (len(ys) == len(fs) == len(params) == n):
         raise ValueError("geoms, ys, fs and params must have the same length")
@@ -284,8 +286,41 @@ def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
     Y = (C.c_void_p * n)(*[_dev(y, "y", g.device, g.proj_shape) for g, y in zip(geoms, ys)])
     F = (C.c_void_p * n)(*[_dev(f, "f", g.device, g.vol_shape) for g, f in zip(geoms, fs)])
     P = (_Params * n)(*[p._c() for p in params])
+    return n, G, Y, F, P
+
+
+def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
+    """TNLM-R on independent problems in one graph replayed n_outer times;
+    every f is updated in place."""
+    n, G, Y, F, P = _batch_args(geoms, ys, fs, params)
     _check(_load().tnlm_reconstruct_batch(n, G, Y, F, P, _stream(stream)), "tnlm_reconstruct_batch")
     return fs
+
+
+class BatchPlan:
+    """One FBS iteration of every problem captured once (tnlm_batch_plan_*);
+    run(k) replays it k times, updating every f in place.  The plan keeps
+    references to the geometries and tensors it was built on."""
+
+    def __init__(self, geoms, ys, fs, params):
+        n, G, Y, F, P = _batch_args(geoms, ys, fs, params)
+        self._keep = (list(geoms), list(ys), list(fs))
+        self.handle = C.c_void_p()
+        _check(_load().tnlm_batch_plan_create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
+
+    def run(self, n_iterations: int, stream=None):
+        _check(_load().tnlm_batch_plan_run(self.handle, int(n_iterations), _stream(stream)), "tnlm_batch_plan_run")
+
+    def close(self):
+        if self.handle:
+            _load().tnlm_batch_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tnlm_enhance(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

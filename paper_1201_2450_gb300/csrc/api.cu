@@ -454,26 +454,28 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
     return timer.finish();
 }
 
-tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
-                                   const tnlm_params *params, void *stream)
+struct tnlm_batch_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// Validate and prepare every problem, then capture one FBS iteration of all of
+// them into *graph: the capture stream forks to up to 8 side streams (problem
+// b on side stream b mod 8) and joins back.
+static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                 const tnlm_params *params, cudaGraph_t *graph)
 {
     if (n < 1 || !geoms || !y || !f || !params) return arg_error("need n >= 1 and non-NULL arrays");
-    const int n_outer = params[0].n_outer;
     for (int b = 0; b < n; ++b) {
-        if (params[b].n_outer != n_outer) return arg_error("all problems of a batch need the same n_outer");
         for (int c = 0; c < b; ++c)
             if (geoms[c] == geoms[b]) return arg_error("a geometry handle may appear once per batch (it owns the workspace)");
         TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1));
     }
-    if (n_outer == 0) return TNLM_OK;
-    cudaStream_t st = as_stream(stream);
     const int ns = n < 8 ? n : 8;  // parallel branches of the graph
     cudaStream_t cs = nullptr;
     std::vector<cudaStream_t> side(ns, nullptr);
     std::vector<cudaEvent_t> join(ns, nullptr);
     cudaEvent_t fork = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     tnlm_status status = TNLM_OK;
     auto cuda_ok = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess && status == TNLM_OK) {
@@ -489,7 +491,6 @@ tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const flo
             cuda_ok(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming), "cudaEventCreate");
         }
     }
-    // capture one iteration of every problem: fork to the side streams, join back
     if (status == TNLM_OK && cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture")) {
         cuda_ok(cudaEventRecord(fork, cs), "cudaEventRecord");
         for (int s = 0; s < ns; ++s) cuda_ok(cudaStreamWaitEvent(side[s], fork, 0), "cudaStreamWaitEvent");
@@ -501,15 +502,13 @@ tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const flo
             cudaEventRecord(join[s], side[s]);
             cudaStreamWaitEvent(cs, join[s], 0);
         }
-        cudaError_t e = cudaStreamEndCapture(cs, &graph);
-        cuda_ok(e, "cudaStreamEndCapture");
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &gr);  // always ends the capture, also after an error
+        if (cuda_ok(e, "cudaStreamEndCapture"))
+            *graph = gr;
+        else if (gr)
+            cudaGraphDestroy(gr);
     }
-    if (status == TNLM_OK && cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate")) {
-        // replays on the caller's stream, after the work already queued there
-        for (int k = 0; k < n_outer && status == TNLM_OK; ++k) cuda_ok(cudaGraphLaunch(exec, st), "cudaGraphLaunch");
-    }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     for (int s = 0; s < ns; ++s) {
         if (join[s]) cudaEventDestroy(join[s]);
         if (side[s]) cudaStreamDestroy(side[s]);
@@ -517,6 +516,70 @@ tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const flo
     if (fork) cudaEventDestroy(fork);
     if (cs) cudaStreamDestroy(cs);
     return status;
+}
+
+tnlm_status tnlm_batch_plan_create(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                   const tnlm_params *params, tnlm_batch_plan **out)
+{
+    if (!out) return arg_error("out must not be NULL");
+    *out = nullptr;
+    cudaGraph_t graph = nullptr;
+    TNLM_TRY(capture_batch(n, geoms, y, f, params, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+        return TNLM_ERR_CUDA;
+    }
+    tnlm_batch_plan *plan = new (std::nothrow) tnlm_batch_plan;
+    if (!plan) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        set_error("out of host memory");
+        return TNLM_ERR_OOM;
+    }
+    plan->graph = graph;
+    plan->exec = exec;
+    *out = plan;
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream)
+{
+    if (!plan) return arg_error("plan must not be NULL");
+    if (n_iterations < 0) return arg_error("n_iterations must be >= 0");
+    cudaStream_t st = as_stream(stream);
+    // replays on the caller's stream, after the work already queued there
+    for (int k = 0; k < n_iterations; ++k) TNLM_TRY_CUDA(cudaGraphLaunch(plan->exec, st));
+    return TNLM_OK;
+}
+
+void tnlm_batch_plan_destroy(tnlm_batch_plan *plan)
+{
+    if (!plan) return;
+    // an executable graph still in flight is freed by the driver when its launches complete
+    cudaGraphExecDestroy(plan->exec);
+    cudaGraphDestroy(plan->graph);
+    delete plan;
+}
+
+tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                   const tnlm_params *params, void *stream)
+{
+    if (n < 1 || !geoms || !y || !f || !params) return arg_error("need n >= 1 and non-NULL arrays");
+    const int n_outer = params[0].n_outer;
+    for (int b = 0; b < n; ++b)
+        if (params[b].n_outer != n_outer) return arg_error("all problems of a batch need the same n_outer");
+    if (n_outer == 0) {
+        for (int b = 0; b < n; ++b) TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1));
+        return TNLM_OK;
+    }
+    tnlm_batch_plan *plan = nullptr;
+    TNLM_TRY(tnlm_batch_plan_create(n, geoms, y, f, params, &plan));
+    const tnlm_status st = tnlm_batch_plan_run(plan, n_outer, stream);
+    tnlm_batch_plan_destroy(plan);
+    return st;
 }
 
 tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *f, const tnlm_params *p, void *stream)

@@ -78,3 +78,18 @@ def test_sweep_argument_checks(lib):
     # weight buffer too small
     assert lib.tnlm_weights(4, 4, 4, 2, vp, 1, 1, 0.1, vp, 10, None) == 1
     assert b"needed" in lib.tnlm_last_error()
+
+
+def test_batch_plan_rejects_bad_arguments(lib):
+    lib = C.CDLL(tnlm.library_path())  # own function objects: the binding's argtypes stay untouched
+    lib.tnlm_last_error.restype = C.c_char_p
+    lib.tnlm_batch_plan_create.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.POINTER(C.c_void_p)]
+    out = C.c_void_p(1)
+    assert lib.tnlm_batch_plan_create(0, None, None, None, None, C.byref(out)) == 1
+    assert out.value is None
+    assert b"n >= 1" in lib.tnlm_last_error()
+    lib.tnlm_batch_plan_run.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+    assert lib.tnlm_batch_plan_run(None, 1, None) == 1
+    lib.tnlm_batch_plan_destroy.argtypes = [C.c_void_p]
+    lib.tnlm_batch_plan_destroy(None)  # NULL is ignored

@@ -542,3 +542,12 @@ def test_reconstruct_batch_graph_equals_single_calls():
     torch.cuda.synchronize()
     for a, b in zip(single, fb):
         assert torch.equal(a, b)
+    # the reusable plan: replays of 2 and then 1 iteration continue from f
+    fp = [cuda(f) for f in f0]
+    plan = tnlm.BatchPlan(Gb, ys, fp, params)
+    plan.run(2)
+    plan.run(1)
+    plan.close()
+    torch.cuda.synchronize()
+    for a, b in zip(single, fp):
+        assert torch.equal(a, b)
