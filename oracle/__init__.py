@@ -83,6 +83,7 @@ def _load():
             "ora_cgls": (None, [G, _dp, _dp, i, C.c_void_p]),
             "ora_fdk": (None, [G, _dp, _dp, C.c_void_p]),
             "ora_energy_grad": (d, [G, _dp, _dp, _dp, i, i, d, d, _dp]),
+            "ora_energy_grad_a": (None, [i, i, i, i, _dp, _dp, i, i, d, _dp]),
             "ora_enhance": (None, [i, i, i, i, _dp, _dp, i, i, d, d, i, i]),
             "ora_num_threads": (i, []),
         }
@@ -217,6 +218,15 @@ def energy_grad(geom: Geometry, y, f, a, d: int, M: int, h: float, mu: float):
     E = _load().ora_energy_grad(geom.ref, _f64(y).reshape(geom.proj_shape), _f64(f).reshape(geom.vol_shape),
                                 _f64(a).reshape(geom.vol_shape), d, M, h, mu, grad)
     return E, grad
+
+
+def energy_grad_a(f, a, d: int, M: int, h: float):
+    """Gradient of 1/2 sum_i J[f_i, f_{i+1}] (weights of Eq. 9 from a) with
+    respect to a, f held fixed: the weights differentiated."""
+    np_, nz, ny, nx = np.shape(f)
+    g = np.empty((np_, nz, ny, nx), np.float64)
+    _load().ora_energy_grad_a(nx, ny, nz, np_, _f64(f).reshape(g.shape), _f64(a).reshape(g.shape), d, M, h, g)
+    return g
 
 
 def fidelity(geom: Geometry, f, y) -> float:

@@ -581,6 +581,68 @@ double ora_energy_grad(const ora_geom *g, const double *yproj, const double *f, 
     return 0.5 * mu * fid + 0.5 * J;
 }
 
+/* Gradient of the TNLM half of the energy, 1/2 sum_i J[f_i, f_{i+1}] (Eq. 2
+ * over the search window, direction-0 weights of Eq. 9), with respect to the
+ * weight-source images a (the weights differentiated; f held fixed).  With
+ * c = 1/(2h^2), w = exp(-c D) / Z and q = (f_i(x) - f_{i+1}(x+delta))^2:
+ *   dJ_x/dD(x,delta) = 1/2 c w(x,delta) (Qbar(x) - q(x,delta)),
+ *   Qbar(x) = sum_delta w(x,delta) q(x,delta),
+ * and D(x,delta) = sum_o (a_i(clamp(x+o)) - a_{i+1}(clamp(x+delta+o)))^2
+ * passes it to both patches (scatter form, every pair visited once).
+ * grad_a is overwritten. */
+void ora_energy_grad_a(int nx, int ny, int nz, int np, const double *f, const double *a, int d, int M, double h,
+                       double *grad_a)
+{
+    const long nvox = (long)nx * ny * nz;
+    const int S = 2 * M + 1, W = S * S * S;
+    const double c = 1.0 / (2.0 * h * h);
+    double *w = (double *)malloc(sizeof(double) * nvox * np * 2 * W);
+    double *q = (double *)malloc(sizeof(double) * W);
+    ora_weights(nx, ny, nz, np, a, d, M, h, w);
+    for (long t = 0; t < nvox * np; ++t) grad_a[t] = 0.0;
+    for (int i = 0; i < np; ++i) {
+        const int j = (i + 1) % np;
+        const double *ai = a + (long)i * nvox, *aj = a + (long)j * nvox;
+        double *gi = grad_a + (long)i * nvox, *gj = grad_a + (long)j * nvox;
+        for (long v = 0; v < nvox; ++v) {
+            const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
+            const double *wv = w + (((long)i * 2 + 0) * nvox + v) * W;
+            double qbar = 0.0;
+            int k = 0;
+            for (int dz = -M; dz <= M; ++dz)
+                for (int dy = -M; dy <= M; ++dy)
+                    for (int dx = -M; dx <= M; ++dx, ++k) {
+                        const int X = x + dx, Y = y + dy, Z = z + dz;
+                        q[k] = 0.0;
+                        if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz) continue;
+                        const double df = f[(long)i * nvox + v] - f[(long)j * nvox + ((long)Z * ny + Y) * nx + X];
+                        q[k] = df * df;
+                        qbar += wv[k] * q[k];
+                    }
+            k = 0;
+            for (int dz = -M; dz <= M; ++dz)
+                for (int dy = -M; dy <= M; ++dy)
+                    for (int dx = -M; dx <= M; ++dx, ++k) {
+                        if (wv[k] == 0.0) continue; /* invalid candidate (or a weight that underflowed) */
+                        const double G = 0.5 * c * wv[k] * (qbar - q[k]);
+                        for (int oz = -d; oz <= d; ++oz)
+                            for (int oy = -d; oy <= d; ++oy)
+                                for (int ox = -d; ox <= d; ++ox) {
+                                    const long pi = ((long)ora_clampi(z + oz, nz) * ny + ora_clampi(y + oy, ny)) * nx +
+                                                    ora_clampi(x + ox, nx);
+                                    const long pj = ((long)ora_clampi(z + dz + oz, nz) * ny +
+                                                     ora_clampi(y + dy + oy, ny)) * nx + ora_clampi(x + dx + ox, nx);
+                                    const double t = 2.0 * G * (ai[pi] - aj[pj]);
+                                    gi[pi] += t;
+                                    gj[pj] -= t;
+                                }
+                    }
+        }
+    }
+    free(q);
+    free(w);
+}
+
 /* sum_i ||P_i f_i - y_i||^2 */
 double ora_fidelity(const ora_geom *g, const double *f, const double *yproj)
 {
