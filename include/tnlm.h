@@ -234,6 +234,24 @@ tnlm_status tnlm_cgls(tnlm_geometry *geom, const float *y, float *x, int n_iter,
 tnlm_status tnlm_energy_grad(tnlm_geometry *geom, const float *y, const float *f, const float *a,
                              const tnlm_params *params, double *energy, float *grad, void *stream);
 
+/* Gradient of the TNLM half of the energy, 1/2 sum_i J[f_i, f_{i+1}] (J of
+ * Eq. 2 over the search window, direction-0 weights of Eq. 9 computed from
+ * a), with respect to the weight-source images a, f held fixed: the
+ * "weights differentiated" part of the energy gradient.  With
+ * c = 1/(2h^2), w = exp(-c D)/Z and q = (f_i(x) - f_{i+1}(x+delta))^2, every
+ * pair contributes dJ/dD = 1/2 c w (sum_delta' w q - q) to both patches of
+ * its distance D (edge-clamped patches, valid window candidates only).
+ * Adding this to the frozen-weight gradient of tnlm_energy_grad called with
+ * a = f gives the gradient of the energy whose weights are computed from f
+ * itself.  f, a, grad_a: [N_p][nz][ny][nx] FP32 device arrays; grad_a is
+ * overwritten and must not alias f or a.  Allocates
+ * (2M+1)^3 (nx ny nz + (nx+2d)(ny+2d)(nz+2d)) floats stream-ordered
+ * (cudaMallocAsync) per call and processes the phase pairs (i, i+1) in
+ * order on `stream`.  The paper minimises Eq. 1 but never differentiates its
+ * weights; this serves gradient-based use of the energy. */
+tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const float *f, const float *a, int d,
+                                     int M, float h, float *grad_a, void *stream);
+
 /* FDK reconstruction (Feldkamp, Davis and Kress, the paper's ref. 16), the
  * initial value f^(0) of TNLM-R and the input g of TNLM-E (Sec. 2.2-2.3):
  * every phase from its own views, assumed to cover a full rotation evenly

@@ -28,7 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
-    "tnlm_energy_grad", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan",
+    "tnlm_energy_grad", "tnlm_energy_grad_weights", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan",
     "reconstruct_host", "library_path",
 ]
 
@@ -116,6 +116,7 @@ def _load():
             "tnlm_fdk": (i, [vp, vp, vp, vp]),
             "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_energy_grad": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
+            "tnlm_energy_grad_weights": (i, [i, i, i, i, vp, vp, i, i, f, vp, vp]),
             "tnlm_reconstruct_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params), vp]),
             "tnlm_batch_plan_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
                                            C.POINTER(vp)]),
@@ -403,22 +404,46 @@ def tnlm_energy_grad(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: torch.
     return E.value, grad
 
 
+def tnlm_energy_grad_weights(f: torch.Tensor, a: torch.Tensor, d: int, M: int, h: float,
+                             grad_a: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Gradient of 1/2 sum J (weights of Eq. 9 from a) with respect to a, f
+    fixed: the weights differentiated."""
+    np_, nz, ny, nx = f.shape
+    if grad_a is None:
+        grad_a = torch.empty_like(f)
+    _check(_load().tnlm_energy_grad_weights(nx, ny, nz, np_, _dev(f, "f"), _dev(a, "a", f.device, f.shape), d, M, h,
+                                            _dev(grad_a, "grad_a", f.device, f.shape), _stream(stream)),
+           "tnlm_energy_grad_weights")
+    return grad_a
+
+
 class TNLMEnergy(torch.autograd.Function):
-    """E(f) of Eq. 1 (J of Eq. 2, weights frozen from a) as an autograd
-    function: the forward pass computes the energy and its gradient with the
-    library's kernels (projector, transpose, TNLM adjoint); the backward pass
-    scales that gradient.  Usage: E = TNLMEnergy.apply(f, geom, y, a, params)."""
+    """E(f, a) of Eq. 1 (J of Eq. 2 with the Eq. 9 weights computed from a)
+    as an autograd function.  The forward pass computes the energy and its
+    gradient in f with the library's kernels (projector, transpose, TNLM
+    adjoint); the backward pass scales it, and when a requires a gradient it
+    adds the gradient through the weights (tnlm_energy_grad_weights).
+    Weights frozen: E = TNLMEnergy.apply(f, geom, y, a.detach(), params);
+    weights differentiated (computed from f itself):
+    E = TNLMEnergy.apply(f, geom, y, f, params)."""
 
     @staticmethod
     def forward(ctx, f, geom, y, a, params):
-        E, grad = tnlm_energy_grad(geom, y, f.detach().contiguous(), a.detach().contiguous(), params)
-        ctx.save_for_backward(grad)
+        fd, ad = f.detach().contiguous(), a.detach().contiguous()
+        E, grad = tnlm_energy_grad(geom, y, fd, ad, params)
+        ctx.save_for_backward(grad, fd, ad)
+        ctx.params = params
         return torch.tensor(E, dtype=torch.float64, device=f.device)
 
     @staticmethod
     def backward(ctx, gE):
-        (grad,) = ctx.saved_tensors
-        return (gE.to(grad.dtype) * grad, None, None, None, None)
+        grad, fd, ad = ctx.saved_tensors
+        g = gE.to(grad.dtype)
+        ga = None
+        if ctx.needs_input_grad[3]:
+            p = ctx.params
+            ga = g * tnlm_energy_grad_weights(fd, ad, p.d, p.M, p.h)
+        return (g * grad if ctx.needs_input_grad[0] else None, None, None, ga, None)
 
 
 def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream=None) -> float:

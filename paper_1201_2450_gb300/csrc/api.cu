@@ -720,6 +720,27 @@ tnlm_status tnlm_energy_grad(tnlm_geometry *geo, const float *y, const float *f,
     return TNLM_OK;
 }
 
+tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
+                                     float h, float *grad_a, void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, 1.0f));
+    if (!f || !a || !grad_a) return arg_error("f, a and grad_a must not be NULL");
+    if (grad_a == f || grad_a == a) return arg_error("grad_a must not alias f or a");
+    cudaStream_t st = as_stream(stream);
+    const size_t n = energy_weights_grad_floats(nx, ny, nz, d, M);
+    float *ws = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), sizeof(float) * n, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocAsync of %zu bytes for the weight-gradient workspace failed", sizeof(float) * n);
+        return TNLM_ERR_OOM;
+    }
+    const tnlm_status s1 = launch_energy_weights_grad(nx, ny, nz, np, f, a, d, M, h, grad_a, ws, st);
+    const cudaError_t e = cudaFreeAsync(ws, st);
+    if (s1 != TNLM_OK) return s1;
+    TNLM_TRY_CUDA(e);
+    return TNLM_OK;
+}
+
 tnlm_status tnlm_fdk(tnlm_geometry *geo, const float *proj, float *vol, void *stream)
 {
     if (!geo || !proj || !vol) return arg_error("geometry, proj and vol must not be NULL");

@@ -166,7 +166,205 @@ __global__ void __launch_bounds__(kNT) k_energy_grad(int nx, int ny, int nz, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of 1/2 sum_i J[f_i, f_{i+1}] through the weights, with respect to
+// the weight-source images a (f fixed).  With c = 1/(2h^2),
+//   G(x,delta) = dJ_x/dD(x,delta) = 1/2 c w(x,delta) (Qbar(x) - q(x,delta)),
+//   Qbar(x) = sum_delta w q,  q = (f_i(x) - f_j(x+delta))^2,  j = i+1,
+// and D(x,delta) = sum_o s(x+o), s(p) = (a_i(cl(p)) - a_j(cl(p+delta)))^2 on
+// the grid padded by d (cl = clamp to the volume).  So, with the box sum
+// B(p,delta) = sum_o G(p-o,delta) over the x inside the volume,
+//   v(p,delta) = 2 B(p,delta) (a_i(cl(p)) - a_j(cl(p+delta))),
+//   grad_i(z) += sum over p with cl(p) = z of sum_delta v(p,delta),
+//   grad_j(z) -= sum over (p,delta) with cl(p+delta) = z of v(p,delta).
+// Per phase pair: k_wa_G writes G[delta][x] (0 for invalid candidates),
+// k_wa_B writes B[delta][p] on the padded grid, k_wa_gather folds both sides
+// back onto the voxels (gathers only; no atomics, deterministic).
+
+__global__ void __launch_bounds__(kNT) k_wa_G(int nx, int ny, int nz, int ntz, const float *__restrict__ ai,
+                                              const float *__restrict__ aj, const float *__restrict__ fi,
+                                              const float *__restrict__ fj, int d, int M, float c2, float cg,
+                                              float *__restrict__ G)
+{
+    extern __shared__ float sm[];
+    const int R = M + d;
+    const int vjx = kTX + 2 * M, vjy = kTY + 2 * M, vjz = kTZ + 2 * M;
+    float *s_ai = sm;
+    float *s_aj = s_ai + (kTX + 2 * d) * (kTY + 2 * d) * (kTZ + 2 * d);
+    float *s_fj = s_aj + (kTX + 2 * R) * (kTY + 2 * R) * (kTZ + 2 * R);
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z, tid = (tz * kTY + ty) * kTX + tx;
+    const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, Z0 = blockIdx.z * kTZ;
+    const long long nvox = (long long)nx * ny * nz;
+    const int x = X0 + tx, y = Y0 + ty, z = Z0 + tz;
+    const bool inside = x < nx && y < ny && z < nz;
+    const long long o = ((long long)clampi(z, nz) * ny + clampi(y, ny)) * nx + clampi(x, nx);
+    const float f0 = __ldg(fi + o);
+    stage(s_ai, ai, X0 - d, Y0 - d, Z0 - d, kTX + 2 * d, kTY + 2 * d, kTZ + 2 * d, nx, ny, nz, tid);
+    stage(s_aj, aj, X0 - R, Y0 - R, Z0 - R, kTX + 2 * R, kTY + 2 * R, kTZ + 2 * R, nx, ny, nz, tid);
+    stage(s_fj, fj, X0 - M, Y0 - M, Z0 - M, vjx, vjy, vjz, nx, ny, nz, tid);
+    __syncthreads();
+    (void)ntz;
+    // pass 1: normaliser and weighted mean of q (online reference as in the sweep)
+    float mref = FLT_MAX, Z = 0.f, S = 0.f;
+    for (int dz = -M; dz <= M; ++dz) {
+        if ((unsigned)(z + dz) >= (unsigned)nz) continue;
+        for (int dy = -M; dy <= M; ++dy) {
+            if ((unsigned)(y + dy) >= (unsigned)ny) continue;
+            for (int dx = -M; dx <= M; ++dx) {
+                if ((unsigned)(x + dx) >= (unsigned)nx) continue;
+                const float t = patch_dist(s_ai, s_aj, tx, ty, tz, dx, dy, dz, d, R) * c2;
+                const float df = f0 - s_fj[((tz + M + dz) * vjy + (ty + M + dy)) * vjx + (tx + M + dx)];
+                if (t < mref - kRescale) {
+                    const float sc = ex2(t - mref);
+                    Z *= sc;
+                    S *= sc;
+                    mref = t;
+                }
+                const float e = ex2(mref - t);
+                Z += e;
+                S = fmaf(e, df * df, S);
+            }
+        }
+    }
+    const float lam = log2f(Z) - mref, qbar = S / Z;
+    // pass 2: G for every window offset (0 where the candidate is outside the volume)
+    int k = 0;
+    for (int dz = -M; dz <= M; ++dz)
+        for (int dy = -M; dy <= M; ++dy)
+            for (int dx = -M; dx <= M; ++dx, ++k) {
+                float g = 0.f;
+                if ((unsigned)(z + dz) < (unsigned)nz && (unsigned)(y + dy) < (unsigned)ny &&
+                    (unsigned)(x + dx) < (unsigned)nx) {
+                    const float t = patch_dist(s_ai, s_aj, tx, ty, tz, dx, dy, dz, d, R) * c2;
+                    const float df = f0 - s_fj[((tz + M + dz) * vjy + (ty + M + dy)) * vjx + (tx + M + dx)];
+                    g = cg * ex2(-t - lam) * (qbar - df * df);
+                }
+                if (inside) G[(long long)k * nvox + ((long long)z * ny + y) * nx + x] = g;
+            }
+}
+
+// B[k][p] = sum over o in [-d,d]^3 with x = p - o inside the volume of G[k][x];
+// p on the padded grid [-d, n+d)^3, stored at (p + d)
+__global__ void __launch_bounds__(256) k_wa_B(int nx, int ny, int nz, int d, int W, const float *__restrict__ G,
+                                              float *__restrict__ B)
+{
+    const int px_n = nx + 2 * d, py_n = ny + 2 * d, pz_n = nz + 2 * d;
+    const long long pn = (long long)px_n * py_n * pz_n;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pn) return;
+    const int px = (int)(t % px_n) - d, py = (int)((t / px_n) % py_n) - d, pz = (int)(t / ((long long)px_n * py_n)) - d;
+    const long long nvox = (long long)nx * ny * nz;
+    const int x0 = max(px - d, 0), x1 = min(px + d, nx - 1);
+    const int y0 = max(py - d, 0), y1 = min(py + d, ny - 1);
+    const int z0 = max(pz - d, 0), z1 = min(pz + d, nz - 1);
+    for (int k = 0; k < W; ++k) {
+        const float *__restrict__ Gk = G + (long long)k * nvox;
+        float b = 0.f;
+        for (int zz = z0; zz <= z1; ++zz)
+            for (int yy = y0; yy <= y1; ++yy) {
+                const float *__restrict__ row = Gk + ((long long)zz * ny + yy) * nx;
+                for (int xx = x0; xx <= x1; ++xx) b += __ldg(row + xx);
+            }
+        B[(long long)k * pn + t] = b;
+    }
+}
+
+// range of padded coordinates p in [-d, n+d) with clamp(p + s) == z (s = 0 for the i side)
+__device__ __forceinline__ void preimage(int z, int s, int n, int d, int &lo, int &hi)
+{
+    lo = (z == 0) ? -d : z - s;
+    hi = (z == n - 1) ? n - 1 + d : z - s;
+    lo = max(lo, -d);
+    hi = min(hi, n - 1 + d);
+}
+
+__global__ void __launch_bounds__(256) k_wa_gather(int nx, int ny, int nz, int d, int M,
+                                                   const float *__restrict__ ai, const float *__restrict__ aj,
+                                                   const float *__restrict__ B, float *__restrict__ gi,
+                                                   float *__restrict__ gj)
+{
+    const long long nvox = (long long)nx * ny * nz;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nvox) return;
+    const int x = (int)(t % nx), y = (int)((t / nx) % ny), z = (int)(t / ((long long)nx * ny));
+    const int px_n = nx + 2 * d, py_n = ny + 2 * d, pz_n = nz + 2 * d;
+    const long long pn = (long long)px_n * py_n * pz_n;
+    const float aiz = __ldg(ai + t), ajz = __ldg(aj + t);
+    float acc_i = 0.f, acc_j = 0.f;
+    int xl, xh, yl, yh, zl, zh;
+    int k = 0;
+    for (int dz = -M; dz <= M; ++dz)
+        for (int dy = -M; dy <= M; ++dy)
+            for (int dx = -M; dx <= M; ++dx, ++k) {
+                const float *__restrict__ Bk = B + (long long)k * pn;
+                // i side: p with clamp(p) = (x, y, z); partner a_j(clamp(p + delta))
+                preimage(x, 0, nx, d, xl, xh);
+                preimage(y, 0, ny, d, yl, yh);
+                preimage(z, 0, nz, d, zl, zh);
+                for (int pz = zl; pz <= zh; ++pz)
+                    for (int py = yl; py <= yh; ++py)
+                        for (int px = xl; px <= xh; ++px) {
+                            const float b = __ldg(Bk + ((long long)(pz + d) * py_n + (py + d)) * px_n + (px + d));
+                            const float aq = __ldg(aj + ((long long)clampi(pz + dz, nz) * ny + clampi(py + dy, ny)) * nx +
+                                                   clampi(px + dx, nx));
+                            acc_i = fmaf(2.f * b, aiz - aq, acc_i);
+                        }
+                // j side: p with clamp(p + delta) = (x, y, z); partner a_i(clamp(p))
+                preimage(x, dx, nx, d, xl, xh);
+                preimage(y, dy, ny, d, yl, yh);
+                preimage(z, dz, nz, d, zl, zh);
+                for (int pz = zl; pz <= zh; ++pz)
+                    for (int py = yl; py <= yh; ++py)
+                        for (int px = xl; px <= xh; ++px) {
+                            const float b = __ldg(Bk + ((long long)(pz + d) * py_n + (py + d)) * px_n + (px + d));
+                            const float ap = __ldg(ai + ((long long)clampi(pz, nz) * ny + clampi(py, ny)) * nx +
+                                                   clampi(px, nx));
+                            acc_j = fmaf(2.f * b, ap - ajz, acc_j);
+                        }
+            }
+    gi[t] += acc_i;
+    gj[t] -= acc_j;
+}
+
 }  // namespace
+
+size_t energy_weights_grad_floats(int nx, int ny, int nz, int d, int M)
+{
+    const size_t W = (size_t)(2 * M + 1) * (2 * M + 1) * (2 * M + 1);
+    return W * ((size_t)nx * ny * nz + (size_t)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d));
+}
+
+tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
+                                       float h, float *grad_a, float *ws, cudaStream_t st)
+{
+    const long long nvox = (long long)nx * ny * nz;
+    const int S = 2 * M + 1, W = S * S * S, R = M + d;
+    float *G = ws, *B = ws + (size_t)W * nvox;
+    const long long pn = (long long)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d);
+    const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    const float cg = (float)(0.5 / (2.0 * (double)h * (double)h));
+    const size_t smem = sizeof(float) * ((size_t)(kTX + 2 * d) * (kTY + 2 * d) * (kTZ + 2 * d) +
+                                         (size_t)(kTX + 2 * R) * (kTY + 2 * R) * (kTZ + 2 * R) +
+                                         (size_t)(kTX + 2 * M) * (kTY + 2 * M) * (kTZ + 2 * M));
+    if (smem > 48 * 1024) TNLM_TRY_CUDA(cudaFuncSetAttribute(k_wa_G, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TNLM_TRY_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(float) * (size_t)np * nvox, st));
+    const int ntz = (nz + kTZ - 1) / kTZ;
+    dim3 block(kTX, kTY, kTZ), grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, ntz);
+    for (int i = 0; i < np; ++i) {
+        const int j = (i + 1) % np;
+        const float *ai = a + (long long)i * nvox, *aj = a + (long long)j * nvox;
+        k_wa_G<<<grid, block, smem, st>>>(nx, ny, nz, ntz, ai, aj, f + (long long)i * nvox, f + (long long)j * nvox, d, M,
+                                          c2, cg, G);
+        TNLM_TRY_CUDA(cudaGetLastError());
+        k_wa_B<<<(unsigned)((pn + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, W, G, B);
+        TNLM_TRY_CUDA(cudaGetLastError());
+        k_wa_gather<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, M, ai, aj, B,
+                                                                    grad_a + (long long)i * nvox,
+                                                                    grad_a + (long long)j * nvox);
+        TNLM_TRY_CUDA(cudaGetLastError());
+    }
+    return TNLM_OK;
+}
 
 long long energy_blocks(int nx, int ny, int nz, int np)
 {

@@ -107,6 +107,11 @@ tnlm_status run_cgls(const CglsArgs &a, cudaStream_t st);
 
 // TNLM part of the energy gradient (energy.cu): lam (np*nvox scratch) <- log-normalisers,
 // grad += TNLM gradient, jpart[energy_blocks()] <- FP64 partials of J.
+// Gradient of 1/2 sum J through the weights w.r.t. their source images a
+// (f fixed); ws holds energy_weights_grad_floats() floats; grad_a overwritten.
+size_t energy_weights_grad_floats(int nx, int ny, int nz, int d, int M);
+tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
+                                       float h, float *grad_a, float *ws, cudaStream_t st);
 tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, const float *f, int d, int M, float h,
                                float *lam, float *grad, double *jpart, cudaStream_t st);
 long long energy_blocks(int nx, int ny, int nz, int np);

@@ -519,6 +519,51 @@ def test_energy_autograd_and_directional_derivatives(ora):
         assert float((gh * v).sum()) == pytest.approx(fd, rel=1e-4)
 
 
+def _weight_grad_inputs(shape, seed):
+    """a: smooth + noise (distances D/2h^2 of order 1 for the h used), f
+    independent of a so that q varies across the window."""
+    a = synth.smooth_volume(shape, seed) + synth.normal(shape, seed + 1, 0.01)
+    f = synth.uniform(shape, seed + 2, 0.0, 0.04)
+    return a, f
+
+
+@pytest.mark.parametrize("shape, d, M, h", [((3, 20, 18, 11), 1, 2, 0.05),  # ragged tiles (8 x 8 x 4)
+                                             ((2, 9, 10, 7), 2, 1, 0.1),     # N_p = 2, d = 2
+                                             ((4, 33, 17, 9), 1, 3, 0.06),   # M = 3
+                                             ((2, 6, 5, 1), 1, 1, 0.05)])    # a single slice
+def test_energy_grad_weights_matches_oracle(ora, shape, d, M, h):
+    """Gradient of 1/2 sum J through the Eq. 9 weights (w.r.t. the weight
+    source a) against the FP64 oracle's scatter form."""
+    a, f = _weight_grad_inputs(shape, 260)
+    ref = ora.energy_grad_a(f, a, d, M, h)
+    got = tnlm.tnlm_energy_grad_weights(cuda(f), cuda(a), d, M, h)
+    assert rel_l2(got.cpu().numpy(), ref) <= RTOL
+
+
+def test_energy_autograd_weights_differentiated(ora):
+    """TNLMEnergy with the weights computed from f itself: f.grad is the
+    frozen-weight gradient plus the gradient through the weights, equal to
+    the oracle's (and, in the oracle, to central differences of E(f))."""
+    geom = GEOMS["c1"]
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    f0 = synth.smooth_volume(G.vol_shape, 262) * 0.02 + synth.uniform(G.vol_shape, 263, 0.0, 0.02)
+    y = synth.uniform(G.proj_shape, 264, 0.0, 0.3)
+    d, M, h, mu = 1, 2, 0.03, 0.7
+    p = tnlm.Params(d=d, M=M, h=h, mu=mu)
+    f = cuda(f0).requires_grad_(True)
+    E = tnlm.TNLMEnergy.apply(f, G, cuda(y), f, p)
+    E.backward()
+    E_ref, gf = ora.energy_grad(OG, y, f0, f0, d, M, h, mu)
+    ref = gf + ora.energy_grad_a(f0, f0, d, M, h)
+    assert float(E.detach()) == pytest.approx(E_ref, rel=1e-5)
+    assert rel_l2(f.grad.cpu().numpy(), ref) <= RTOL
+    # frozen: a detached gives the f-gradient alone
+    f2 = cuda(f0).requires_grad_(True)
+    tnlm.TNLMEnergy.apply(f2, G, cuda(y), f2.detach(), p).backward()
+    assert rel_l2(f2.grad.cpu().numpy(), gf) <= RTOL
+
+
 def test_reconstruct_batch_graph_equals_single_calls():
     """Uneven problems in one captured graph replayed n_outer times give the
     same images, bit for bit, as separate tnlm_reconstruct calls."""
