@@ -252,6 +252,30 @@ tnlm_status tnlm_energy_grad(tnlm_geometry *geom, const float *y, const float *f
 tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const float *f, const float *a, int d,
                                      int M, float h, float *grad_a, void *stream);
 
+/* Launch-shape autotuning (no counterpart in the paper; it serves speed
+ * only).  Several launch shapes of the hot kernels are compiled: projector
+ * blocks of 32 x {2,4,8} pixels, band-transpose blocks of 32 x {2,4} voxel
+ * columns with {4,8} z cells per thread, and 4 warp layouts of the box-sum
+ * sweep.  Every shape computes each output with the same operations in the
+ * same order, so results do not depend on the choice.
+ * tnlm_autotune times each shape on the handle's problem size (synthetic
+ * inputs in stream-ordered scratch, one warm-up and the best of two timed
+ * launches), keeps the fastest projector and transpose shapes in the handle
+ * and the fastest FP32 sweep shape for (params->d, params->M) in a
+ * process-wide table, and writes {projector rows, transpose cells, transpose
+ * rows, sweep shape} to choice[4] (nullable).  It synchronises `stream` and
+ * uses the handle's workspace, so call it before capturing a graph and not
+ * while other calls on the handle are queued.
+ * tnlm_autotune_sweep does the same for the sweep alone (bf16 != 0: the BF16
+ * storage kernels), writing the chosen shape to *shape (nullable).
+ * tnlm_set_launch_shapes / tnlm_set_sweep_shape set a shape directly
+ * (TNLM_ERR_ARG for a shape that is not compiled). */
+tnlm_status tnlm_autotune(tnlm_geometry *geom, const tnlm_params *params, int *choice, void *stream);
+tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int n_phases, int d, int M, float h, int bf16, int *shape,
+                                void *stream);
+tnlm_status tnlm_set_launch_shapes(tnlm_geometry *geom, int projector_rows, int transpose_cells, int transpose_rows);
+tnlm_status tnlm_set_sweep_shape(int d, int M, int bf16, int shape);
+
 /* FDK reconstruction (Feldkamp, Davis and Kress, the paper's ref. 16), the
  * initial value f^(0) of TNLM-R and the input g of TNLM-E (Sec. 2.2-2.3):
  * every phase from its own views, assumed to cover a full rotation evenly

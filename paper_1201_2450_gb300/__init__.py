@@ -29,6 +29,7 @@ __all__ = [
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
     "tnlm_energy_grad", "tnlm_energy_grad_weights", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan",
+    "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path",
 ]
 
@@ -122,6 +123,10 @@ def _load():
                                            C.POINTER(vp)]),
             "tnlm_batch_plan_run": (i, [vp, i, vp]),
             "tnlm_batch_plan_destroy": (None, [vp]),
+            "tnlm_autotune": (i, [vp, C.POINTER(_Params), C.POINTER(C.c_int), vp]),
+            "tnlm_autotune_sweep": (i, [i, i, i, i, i, i, f, i, C.POINTER(C.c_int), vp]),
+            "tnlm_set_launch_shapes": (i, [vp, i, i, i]),
+            "tnlm_set_sweep_shape": (i, [i, i, i, i]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -296,6 +301,34 @@ def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
     n, G, Y, F, P = _batch_args(geoms, ys, fs, params)
     _check(_load().tnlm_reconstruct_batch(n, G, Y, F, P, _stream(stream)), "tnlm_reconstruct_batch")
     return fs
+
+
+def tnlm_autotune(geom: Geometry, params: Params, stream=None) -> dict:
+    """Time the compiled launch shapes on this problem and keep the fastest
+    (projector and transpose shapes in the handle, the FP32 sweep shape for
+    (d, M) process-wide).  Results do not depend on the choice."""
+    out = (C.c_int * 4)()
+    p = params._c()
+    _check(_load().tnlm_autotune(geom.handle, C.byref(p), out, _stream(stream)), "tnlm_autotune")
+    return {"projector_rows": out[0], "transpose_cells": out[1], "transpose_rows": out[2], "sweep_shape": out[3]}
+
+
+def tnlm_autotune_sweep(shape, d: int, M: int, h: float, bf16: bool = False, stream=None) -> int:
+    """Tune the box-sum sweep for a [N_p, nz, ny, nx] problem; returns the shape index."""
+    np_, nz, ny, nx = shape
+    out = C.c_int()
+    _check(_load().tnlm_autotune_sweep(nx, ny, nz, np_, d, M, h, int(bool(bf16)), C.byref(out), _stream(stream)),
+           "tnlm_autotune_sweep")
+    return out.value
+
+
+def tnlm_set_launch_shapes(geom: Geometry, projector_rows: int, transpose_cells: int, transpose_rows: int):
+    _check(_load().tnlm_set_launch_shapes(geom.handle, projector_rows, transpose_cells, transpose_rows),
+           "tnlm_set_launch_shapes")
+
+
+def tnlm_set_sweep_shape(d: int, M: int, bf16: bool, shape: int):
+    _check(_load().tnlm_set_sweep_shape(d, M, int(bool(bf16)), shape), "tnlm_set_sweep_shape")
 
 
 class BatchPlan:

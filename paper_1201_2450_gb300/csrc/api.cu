@@ -46,14 +46,14 @@ static tnlm_status dev_alloc(T **p, size_t count)
     return TNLM_OK;
 }
 
-static tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars)
+tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars)
 {
     const KGeom &kg = g->kg;
     TNLM_TRY(dev_alloc(&g->d_r, (size_t)g->n_views_total * kg.npix));
     TNLM_TRY(dev_alloc(&g->d_g, (size_t)kg.np * kg.nvox));
     if (need_tmp) TNLM_TRY(dev_alloc(&g->d_tmp, (size_t)kg.np * kg.nvox));
     if (!g->d_part) {
-        long long n = forward_blocks(kg, g->n_views_total);
+        long long n = forward_blocks_max(kg, g->n_views_total);
         if (n < sumsq_scratch_len()) n = sumsq_scratch_len();
         TNLM_TRY(dev_alloc(&g->d_part, (size_t)n));
         g->part_len = n;
@@ -93,7 +93,7 @@ static tnlm_status ensure_cgls_workspace(tnlm_geometry *g)
 // Column prefix sums for the band transpose: allocated on first use when the
 // geometry admits that transpose; if the allocation fails the exact per-cell
 // transpose runs instead (same results, slower).
-static float *prefix_workspace(tnlm_geometry *g)
+float *prefix_workspace(tnlm_geometry *g)
 {
     if (!bands_apply(g->kg)) return nullptr;
     if (!g->d_pref) {
@@ -253,6 +253,9 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry *
     k.alpha0 = (float)(d.sad / d.sdd);
     k.nvox = (long long)d.nx * d.ny * d.nz;
     k.npix = (long long)d.nu * d.nv;
+    k.fwd_by = 4;
+    k.bp_by = 4;
+    k.bp_ch = 8;
     g->n_views_total = (int)total;
     g->n_views.assign(d.n_views, d.n_views + d.n_phases);
     g->angles.assign(d.angles_rad, d.angles_rad + total);

@@ -20,9 +20,9 @@
 namespace tnlm {
 namespace {
 
-constexpr int kFwdBX = 32, kFwdBY = 4;        // projector block: 32 u x 4 v pixels
-constexpr int kBpBX = 32, kBpBY = 4, kBpCH = 8;  // transpose block: 32 x 4 columns, 8 voxels in z each
-constexpr int kBandCH = 8;                        // z cells per thread in the band transpose
+constexpr int kFwdBX = 32;                       // projector block: 32 u x BY v pixels (BY in {2, 4, 8})
+constexpr int kBpBX = 32, kBpBY = 4, kBpCH = 8;  // exact transpose block: 32 x 4 columns, 8 voxels in z each
+// band transpose: 32 x BY columns (BY in {2, 4}), CH z cells per thread (CH in {4, 8})
 
 // Enter the slab 0 <= E + b G < n (voxel-index units) into [blo, bhi];
 // a ray parallel to the slab is inside iff 0 <= E < n (half-open cells).
@@ -74,23 +74,28 @@ __device__ __forceinline__ int clamp_floor(float x, int n)
     return (int)floorf(x);
 }
 
-__device__ __forceinline__ double block_sum_128(double v, double *ws)
+// sum over a block of NW warps (fixed order)
+template <int NW>
+__device__ __forceinline__ double block_sum_warps(double v, double *ws)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if ((tid & 31) == 0) ws[tid >> 5] = v;
     __syncthreads();
-    return ws[0] + ws[1] + ws[2] + ws[3];
+    double s = ws[0];
+#pragma unroll
+    for (int k = 1; k < NW; ++k) s += ws[k];
+    return s;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kFwdBX *kFwdBY)
+template <int MODE, int BY>
+__global__ void __launch_bounds__(kFwdBX *BY)
     k_forward(KGeom G, const ViewGeom *__restrict__ views, const float *__restrict__ vol,
               const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials)
 {
-    __shared__ double ws[4];
+    __shared__ double ws[BY];
     const int iu = blockIdx.x * kFwdBX + threadIdx.x;
-    const int iv = blockIdx.y * kFwdBY + threadIdx.y;
+    const int iv = blockIdx.y * BY + threadIdx.y;
     const int vg = blockIdx.z;
     const ViewGeom V = views[vg];
     double r2 = 0.0;
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kFwdBX *kFwdBY)
         }
     }
     if (MODE == 1) {
-        const double s = block_sum_128(r2, ws);
+        const double s = block_sum_warps<BY>(r2, ws);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
     }
@@ -383,13 +388,13 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
 // and m; (ii) full rows between two bands, whose chord stays inside one cell:
 // they add r |D| dg each, summed with two prefix-sum loads.  Equal to the
 // per-cell exact tests of k_backproject up to rounding.
-template <bool SCALED, int CH>
-__global__ void __launch_bounds__(kBpBX *kBpBY, 10)
+template <bool SCALED, int CH, int BY>
+__global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
     k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
                         const float *__restrict__ proj, const float2 *__restrict__ pref, const float *vin,
                         float *vout, float alpha, float beta, int nchunks)
 {
-    constexpr int NT = kBpBX * kBpBY;
+    constexpr int NT = kBpBX * BY;
     extern __shared__ float4 sm4[];
     float4 *s_row = sm4;  // per detector row: (v, 1/v or 0, v^2, 0)
     const int tid = threadIdx.y * kBpBX + threadIdx.x;
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
     }
     __syncthreads();
     const int ix = blockIdx.x * kBpBX + threadIdx.x;
-    const int iy = blockIdx.y * kBpBY + threadIdx.y;
+    const int iy = blockIdx.y * BY + threadIdx.y;
     const int phase = blockIdx.z / nchunks;
     const int iz0 = (blockIdx.z % nchunks) * CH;
     if (ix >= G.nx || iy >= G.ny) return;
@@ -514,18 +519,38 @@ __global__ void __launch_bounds__(kBpBX *kBpBY, 10)
 
 long long forward_blocks(const KGeom &kg, int n_views_total)
 {
-    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + kFwdBY - 1) / kFwdBY) * n_views_total;
+    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + kg.fwd_by - 1) / kg.fwd_by) * n_views_total;
+}
+
+long long forward_blocks_max(const KGeom &kg, int n_views_total)
+{
+    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + 1) / 2) * n_views_total;  // smallest BY = 2
+}
+
+template <int MODE, int BY>
+static void launch_forward_by(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
+                              const float *y, float *out, double *partials, cudaStream_t st)
+{
+    dim3 grid((kg.nu + kFwdBX - 1) / kFwdBX, (kg.nv + BY - 1) / BY, n_views_total);
+    k_forward<MODE, BY><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views, vol, y, out, partials);
 }
 
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
                            const float *y, float *out, double *partials, int mode, cudaStream_t st)
 {
-    dim3 block(kFwdBX, kFwdBY);
-    dim3 grid((kg.nu + kFwdBX - 1) / kFwdBX, (kg.nv + kFwdBY - 1) / kFwdBY, n_views_total);
-    if (mode == 0)
-        k_forward<0><<<grid, block, 0, st>>>(kg, views, vol, nullptr, out, nullptr);
-    else
-        k_forward<1><<<grid, block, 0, st>>>(kg, views, vol, y, out, partials);
+    if (kg.fwd_by != 2 && kg.fwd_by != 4 && kg.fwd_by != 8) {
+        set_error("projector block rows must be 2, 4 or 8 (got %d)", kg.fwd_by);
+        return TNLM_ERR_ARG;
+    }
+    if (mode == 0) {
+        if (kg.fwd_by == 2) launch_forward_by<0, 2>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+        else if (kg.fwd_by == 4) launch_forward_by<0, 4>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+        else launch_forward_by<0, 8>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+    } else {
+        if (kg.fwd_by == 2) launch_forward_by<1, 2>(kg, views, n_views_total, vol, y, out, partials, st);
+        else if (kg.fwd_by == 4) launch_forward_by<1, 4>(kg, views, n_views_total, vol, y, out, partials, st);
+        else launch_forward_by<1, 8>(kg, views, n_views_total, vol, y, out, partials, st);
+    }
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
 }
@@ -545,6 +570,23 @@ size_t prefix_floats(const KGeom &kg, int n_views_total)
     return (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu + (size_t)n_views_total * kg.npix;
 }
 
+template <int CH, int BY>
+static tnlm_status launch_bands(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *src,
+                                const float2 *pref, const float *vin, float *vout, float alpha, float beta,
+                                cudaStream_t st)
+{
+    const int nchb = (kg.nz + CH - 1) / CH;
+    dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + BY - 1) / BY, kg.np * nchb);
+    const size_t smem = sizeof(float4) * kg.nv;
+    if (smem > 48 * 1024)
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CH, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    k_backproject_bands<true, CH, BY><<<grid, dim3(kBpBX, BY), smem, st>>>(kg, views, view_off, src, pref, vin, vout,
+                                                                            alpha, beta, nchb);
+    TNLM_TRY_CUDA(cudaGetLastError());
+    return TNLM_OK;
+}
+
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
                                const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
                                int n_views_total, cudaStream_t st)
@@ -553,9 +595,6 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
     dim3 block(kBpBX, kBpBY);
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchunks);
     if (pref_ws && bands_apply(kg)) {
-        constexpr int CHB = kBandCH;
-        const int nchb = (kg.nz + CHB - 1) / CHB;
-        dim3 gridb((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + kBpBY - 1) / kBpBY, kg.np * nchb);
         float2 *pref = reinterpret_cast<float2 *>(pref_ws);
         float *rtil = pref_ws + (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu;  // unscaled input: r |D| copy
         dim3 sg((kg.nu + 255) / 256, n_views_total);
@@ -564,12 +603,19 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
         else
             k_colscan<false><<<sg, 256, 0, st>>>(kg, proj, pref, rtil);
         TNLM_TRY_CUDA(cudaGetLastError());
-        const size_t smem = sizeof(float4) * kg.nv;
-        if (smem > 48 * 1024)
-            TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_backproject_bands<true, CHB><<<gridb, block, smem, st>>>(kg, views, view_off, scaled ? proj : rtil, pref, vin,
-                                                                    vout, alpha, beta, nchb);
-        TNLM_TRY_CUDA(cudaGetLastError());
+        const float *src = scaled ? proj : rtil;
+        if (kg.bp_ch == 8 && kg.bp_by == 4)
+            TNLM_TRY((launch_bands<8, 4>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+        else if (kg.bp_ch == 8 && kg.bp_by == 2)
+            TNLM_TRY((launch_bands<8, 2>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+        else if (kg.bp_ch == 4 && kg.bp_by == 4)
+            TNLM_TRY((launch_bands<4, 4>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+        else if (kg.bp_ch == 4 && kg.bp_by == 2)
+            TNLM_TRY((launch_bands<4, 2>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+        else {
+            set_error("band transpose shape must be CH in {4, 8} and BY in {2, 4} (got %d, %d)", kg.bp_ch, kg.bp_by);
+            return TNLM_ERR_ARG;
+        }
         return TNLM_OK;
     }
     const size_t smem = sizeof(float4) * kg.nv + sizeof(float) * kBpCH * kBpBX * kBpBY;

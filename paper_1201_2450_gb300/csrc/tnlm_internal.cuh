@@ -25,6 +25,10 @@ struct KGeom {
     float alpha0;            // sad / sdd: ray parameter of the isocentre plane
     long long nvox;          // nx*ny*nz
     long long npix;          // nu*nv
+    // launch shapes (defaults 4, 4, 8; chosen by tnlm_autotune)
+    int fwd_by;              // projector block rows: 2, 4 or 8
+    int bp_by;               // band transpose block rows: 2 or 4
+    int bp_ch;               // band transpose z cells per thread: 4 or 8
 };
 
 // One projection view: rotation and owning phase.
@@ -57,6 +61,7 @@ void set_error(const char *fmt, ...);
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
                            const float *y, float *out, double *partials, int mode, cudaStream_t st);
 long long forward_blocks(const KGeom &kg, int n_views_total);
+long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
 
 // vout = beta * vin + alpha * P^T proj.  scaled: proj already multiplied by
 // the ray length |source -> pixel| (the residual form written by mode 1).
@@ -123,6 +128,30 @@ int cgls_partial_len(int np);
 
 tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float h, float mu);
 
+// Box-sum sweep launch shapes (sweep_box.cuh); each returns false when (d, M)
+// has no box kernel.  box_shape / set_box_shape hold the process-wide choice
+// per (d, M, storage) that tnlm_autotune makes.
+constexpr int kBoxShapes = 4;
+int box_shape(int d, int M, int bf16);
+void set_box_shape(int d, int M, int bf16, int v);
+bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,
+                      const float *g, float *out, float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);
+bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,
+                           const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu, int clip,
+                           cudaStream_t st, cudaError_t *err);
+#define TNLM_BOX_DECL(V)                                                                                          \
+    bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,    \
+                           const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,            \
+                           cudaError_t *err);                                                                     \
+    bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,           \
+                                  const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu,     \
+                                  int clip, cudaStream_t st, cudaError_t *err);
+TNLM_BOX_DECL(0)
+TNLM_BOX_DECL(1)
+TNLM_BOX_DECL(2)
+TNLM_BOX_DECL(3)
+#undef TNLM_BOX_DECL
+
 }  // namespace tnlm
 
 // The opaque handle.
@@ -158,3 +187,11 @@ struct tnlm_geometry {
     double stage_ms[3] = {0, 0, 0};
     long long stage_launches[3] = {0, 0, 0};
 };
+
+namespace tnlm {
+// Workspace of a geometry handle (api.cu): r, g, FP64 partials and scalars;
+// the band-transpose prefix array (nullptr when the geometry does not admit
+// that transpose or the allocation failed).
+tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars);
+float *prefix_workspace(tnlm_geometry *g);
+}  // namespace tnlm

@@ -93,3 +93,13 @@ def test_batch_plan_rejects_bad_arguments(lib):
     assert lib.tnlm_batch_plan_run(None, 1, None) == 1
     lib.tnlm_batch_plan_destroy.argtypes = [C.c_void_p]
     lib.tnlm_batch_plan_destroy(None)  # NULL is ignored
+
+
+def test_launch_shape_setters_reject_uncompiled_shapes(lib):
+    lib = C.CDLL(tnlm.library_path())
+    lib.tnlm_last_error.restype = C.c_char_p
+    assert lib.tnlm_set_sweep_shape(1, 3, 0, 4) == 1
+    assert b"shape" in lib.tnlm_last_error()
+    assert lib.tnlm_set_sweep_shape(5, 3, 0, 0) == 1
+    lib.tnlm_set_launch_shapes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    assert lib.tnlm_set_launch_shapes(None, 4, 8, 4) == 1
