@@ -48,10 +48,10 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
     # the transpose stage is the column scan plus the band kernel
-    "k_forward": {"bytes_per_launch": int((271.968256e6 + 148.052992e6) * 10 / 6), "source_sha": "983c825a053aa4ca"},
-    "k_backproject": {"bytes_per_launch": int((169.98144e6 + 285.81632e6 + 556.105728e6 + 92.62976e6) * 10 / 6),
-                      "source_sha": "983c825a053aa4ca"},
-    "k_sweep": {"bytes_per_launch": int((162.723328e6 + 84.157952e6) * 10 / 6), "source_sha": "551f684abbbc1a01"},
+    "k_forward": {"bytes_per_launch": int((271.703552e6 + 147.8272e6) * 10 / 6), "source_sha": "d98d64215d275221"},
+    "k_backproject": {"bytes_per_launch": int((169.89824e6 + 285.024512e6 + 557.616896e6 + 93.241856e6) * 10 / 6),
+                      "source_sha": "d98d64215d275221"},
+    "k_sweep": {"bytes_per_launch": int((161.970944e6 + 83.84768e6) * 10 / 6), "source_sha": "4e8b41aeca19e017"},
 }
 
 
@@ -60,7 +60,7 @@ def _src_sha(fname: str) -> str:
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-KERNEL_SRC = {"k_forward": "projector.cu", "k_backproject": "projector.cu", "k_sweep": "tnlm_sweep.cu"}
+KERNEL_SRC = {"k_forward": "projector.cu", "k_backproject": "projector.cu", "k_sweep": "sweep_box.cuh"}
 
 
 def measured_peaks() -> dict:
@@ -293,7 +293,7 @@ def run_ours(args, rank, world, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = e_steps * world / e2e_s
 
-    variants = {} if args.no_variants else measure_variants(tnlm, synth, geom, y, stream)
+    variants = {} if args.no_variants else measure_variants(tnlm, synth, geom, y, stream, params)
 
     peaks = measured_peaks()
     names = ["k_forward", "k_backproject", "k_sweep"]
@@ -372,7 +372,7 @@ def _time_ms(fn, stream, reps=3):
     return statistics.median(out)
 
 
-def measure_variants(tnlm, synth, geom, y, stream) -> dict:
+def measure_variants(tnlm, synth, geom, y, stream, params) -> dict:
     """Steps either side of the FBS iteration and the enhancement workload:
     FDK of all phases, one CGLS iteration of (P1), and TNLM-E on
     10 x 512x512x128 (d = 2, M = 3, h = 0.04) in FP32."""
@@ -386,6 +386,27 @@ def measure_variants(tnlm, synth, geom, y, stream) -> dict:
     ms0 = _time_ms(lambda: tnlm.tnlm_cgls(geom, y, x0, 0), stream)
     out["cgls_ms_per_iteration"] = round((ms - ms0) / n_it, 3)
     out["cgls_setup_ms"] = round(ms0, 3)
+    # TNLM-R with BF16 storage on the same workload (3 iterations from 0 against the FP32 result)
+    p3 = tnlm.Params(d=params.d, M=params.M, h=params.h, mu=params.mu, tau=params.tau, n_outer=3, clip_nonneg=1)
+    y16 = y.bfloat16()
+    f16 = torch.zeros(geom.vol_shape, device="cuda", dtype=torch.bfloat16)
+    f32 = torch.zeros(geom.vol_shape, device="cuda")
+
+    def r16():
+        f16.zero_()
+        tnlm.tnlm_reconstruct_bf16(geom, y16, f16, p3)
+
+    def r32():
+        f32.zero_()
+        tnlm.tnlm_reconstruct(geom, y, f32, p3)
+
+    ms16 = _time_ms(r16, stream)
+    ms32 = _time_ms(r32, stream)
+    out["bf16_recon_ms_per_iteration"] = round(ms16 / 3, 3)
+    out["fp32_recon_ms_per_iteration_same_run"] = round(ms32 / 3, 3)
+    out["bf16_recon_rel_l2_vs_fp32_3_iterations"] = float(
+        f"{float(torch.linalg.vector_norm((f16.float() - f32).double()) / torch.linalg.vector_norm(f32.double())):.3e}")
+    del y16, f16, f32
     c3 = synth.C3
     g, _ = synth.enhance_input(c3, device="cuda")
     f = torch.empty_like(g)
@@ -465,33 +486,56 @@ def batch_configs(n: int = 16, seed: int = 1005):
 
 
 def measure_batch(tnlm, synth, stream, n_outer: int = 3) -> dict:
+    """16 uneven problems: sequential tnlm_reconstruct calls against one
+    captured plan replayed n_outer times, in FP32 and in BF16 storage, with
+    launch shapes tuned per problem first; BF16 error = max over problems of
+    rel-L2 against the FP32 result (the FP32 path is within 1e-5 of the FP64
+    oracle in the parity tests)."""
     cfgs = batch_configs()
     probs = [synth.recon_problem(c, device="cuda") for c in cfgs]
     geoms = [tnlm.Geometry(pb.geom) for pb in probs]
     ys = [pb.y.contiguous() for pb in probs]
     params = [tnlm.Params(d=c.d, M=c.M, h=c.h, mu=c.mu, tau=2e-6, n_outer=n_outer) for c in cfgs]
+    for g, p in zip(geoms, params):
+        tnlm.tnlm_autotune(g, p)
     fs = [torch.zeros(g.vol_shape, device="cuda") for g in geoms]
 
     def seq():
         for g, y, f, p in zip(geoms, ys, fs, params):
+            f.zero_()
             tnlm.tnlm_reconstruct(g, y, f, p)
 
-    def batch():
-        tnlm.tnlm_reconstruct_batch(geoms, ys, fs, params)
-
     seq_ms = _time_ms(seq, stream, reps=1)
-    bat_ms = _time_ms(batch, stream, reps=1)
+    plan = tnlm.BatchPlan(geoms, ys, fs, params)
+
+    def run_plan(pl, xs):
+        for x in xs:
+            x.zero_()
+        pl.run(n_outer)
+
+    bat_ms = _time_ms(lambda: run_plan(plan, fs), stream, reps=1)
+    plan.close()
+    ys16 = [y.bfloat16() for y in ys]
+    fs16 = [torch.zeros(g.vol_shape, device="cuda", dtype=torch.bfloat16) for g in geoms]
+    plan16 = tnlm.BatchPlan(geoms, ys16, fs16, params)
+    b16_ms = _time_ms(lambda: run_plan(plan16, fs16), stream, reps=1)
+    plan16.close()
+    err16 = max(float(torch.linalg.vector_norm((a.float() - b).double()) / torch.linalg.vector_norm(b.double()))
+                for a, b in zip(fs16, fs))
     n_it = n_outer * len(cfgs)
     voxels = sum(c.n_phases * c.vol[0] * c.vol[1] * c.vol[2] for c in cfgs)
     res = {"batch16_workload": "16 uneven TNLM-R problems (6-10 phases, 128^2x48..256^2x96, 20-60 views/phase, "
-                               "384x288 or 512x384), 3 FBS iterations each, FP32",
+                               f"384x288 or 512x384), {n_outer} FBS iterations each, autotuned launch shapes",
            "batch16_total_voxels": voxels,
            "batch16_graph_ms": round(bat_ms, 2), "batch16_sequential_ms": round(seq_ms, 2),
            "batch16_graph_problem_iterations_per_s": round(n_it / (bat_ms / 1e3), 3),
-           "batch16_sequential_problem_iterations_per_s": round(n_it / (seq_ms / 1e3), 3)}
+           "batch16_sequential_problem_iterations_per_s": round(n_it / (seq_ms / 1e3), 3),
+           "batch16_bf16_graph_ms": round(b16_ms, 2),
+           "batch16_bf16_graph_problem_iterations_per_s": round(n_it / (b16_ms / 1e3), 3),
+           "batch16_bf16_max_rel_l2_vs_fp32": float(f"{err16:.3e}")}
     for g in geoms:
         g.close()
-    del probs, ys, fs
+    del probs, ys, fs, ys16, fs16
     torch.cuda.empty_cache()
     return res
 

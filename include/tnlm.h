@@ -145,6 +145,19 @@ tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float 
 tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, const tnlm_params *params,
                              double *report, void *stream);
 
+/* TNLM-R with BF16 storage and FP32 arithmetic: y ([sum n_views][nv][nu])
+ * and f ([N_p][nz][ny][nx]) are bfloat16 bit patterns, and so are the
+ * handle's g^(k) image and sweep scratch (in its FP32-sized workspace).
+ * Every value is widened to FP32 when read; ray sums, the residual (kept
+ * FP32 in the workspace), transposes, patch distances, weights and
+ * normalisers are FP32; the gradient step and every sweep round their
+ * outputs to BF16 once (round to nearest even); reductions are FP64.  Same
+ * parameters as tnlm_reconstruct except: (P1) by gradient steps only
+ * (p1_solver = 1 gives TNLM_ERR_NOT_IMPLEMENTED) and d in {1,2}, M in
+ * {1,2,3} (the box-sum sweep). */
+tnlm_status tnlm_reconstruct_bf16(tnlm_geometry *geom, const uint16_t *y, uint16_t *f, const tnlm_params *params,
+                                  double *report, void *stream);
+
 /* TNLM-R for a batch of independent problems (uneven sizes, phase counts
  * and view counts allowed) in one CUDA graph: one FBS iteration of every
  * problem is captured (problems on parallel graph branches) and the graph
@@ -169,6 +182,9 @@ typedef struct tnlm_batch_plan tnlm_batch_plan;
 tnlm_status tnlm_batch_plan_create(int n_problems, tnlm_geometry *const *geoms, const float *const *y,
                                    float *const *f, const tnlm_params *params, tnlm_batch_plan **out);
 tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream);
+/* The same plan for problems stored in BF16 (as tnlm_reconstruct_bf16). */
+tnlm_status tnlm_batch_plan_create_bf16(int n_problems, tnlm_geometry *const *geoms, const uint16_t *const *y,
+                                        uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out);
 void tnlm_batch_plan_destroy(tnlm_batch_plan *plan);
 
 /* TNLM-E (Sec. 2.3): f^(0) = g, then params->n_outer sweeps of (weights of

@@ -28,7 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
-    "tnlm_energy_grad", "tnlm_energy_grad_weights", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan",
+    "tnlm_energy_grad", "tnlm_energy_grad_weights", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path",
 ]
@@ -122,6 +122,9 @@ def _load():
             "tnlm_batch_plan_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
                                            C.POINTER(vp)]),
             "tnlm_batch_plan_run": (i, [vp, i, vp]),
+            "tnlm_batch_plan_create_bf16": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
+                                                C.POINTER(vp)]),
+            "tnlm_reconstruct_bf16": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_batch_plan_destroy": (None, [vp]),
             "tnlm_autotune": (i, [vp, C.POINTER(_Params), C.POINTER(C.c_int), vp]),
             "tnlm_autotune_sweep": (i, [i, i, i, i, i, i, f, i, C.POINTER(C.c_int), vp]),
@@ -284,13 +287,13 @@ def tnlm_reconstruct(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: P
     return f, rep
 
 
-def _batch_args(geoms, ys, fs, params):
+def _batch_args(geoms, ys, fs, params, dtype=torch.float32):
     n = len(geoms)
     if not (len(ys) == len(fs) == len(params) == n):
         raise ValueError("geoms, ys, fs and params must have the same length")
     G = (C.c_void_p * n)(*[g.handle.value for g in geoms])
-    Y = (C.c_void_p * n)(*[_dev(y, "y", g.device, g.proj_shape) for g, y in zip(geoms, ys)])
-    F = (C.c_void_p * n)(*[_dev(f, "f", g.device, g.vol_shape) for g, f in zip(geoms, fs)])
+    Y = (C.c_void_p * n)(*[_dev(y, "y", g.device, g.proj_shape, dtype) for g, y in zip(geoms, ys)])
+    F = (C.c_void_p * n)(*[_dev(f, "f", g.device, g.vol_shape, dtype) for g, f in zip(geoms, fs)])
     P = (_Params * n)(*[p._c() for p in params])
     return n, G, Y, F, P
 
@@ -301,6 +304,19 @@ def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
     n, G, Y, F, P = _batch_args(geoms, ys, fs, params)
     _check(_load().tnlm_reconstruct_batch(n, G, Y, F, P, _stream(stream)), "tnlm_reconstruct_batch")
     return fs
+
+
+def tnlm_reconstruct_bf16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: Params, report: bool = False,
+                          stream=None):
+    """TNLM-R in place on bfloat16 f from bfloat16 y, FP32 arithmetic;
+    returns (f, report or None)."""
+    rep = np.zeros((params.n_outer, params.n_inner), np.float64) if report else None
+    p = params._c()
+    _check(_load().tnlm_reconstruct_bf16(geom.handle, _dev(y, "y", geom.device, geom.proj_shape, torch.bfloat16),
+                                         _dev(f, "f", geom.device, geom.vol_shape, torch.bfloat16), C.byref(p),
+                                         rep.ctypes.data if rep is not None else None, _stream(stream)),
+           "tnlm_reconstruct_bf16")
+    return f, rep
 
 
 def tnlm_autotune(geom: Geometry, params: Params, stream=None) -> dict:
@@ -337,10 +353,12 @@ class BatchPlan:
     references to the geometries and tensors it was built on."""
 
     def __init__(self, geoms, ys, fs, params):
-        n, G, Y, F, P = _batch_args(geoms, ys, fs, params)
+        bf16 = len(fs) > 0 and fs[0].dtype == torch.bfloat16
+        n, G, Y, F, P = _batch_args(geoms, ys, fs, params, torch.bfloat16 if bf16 else torch.float32)
         self._keep = (list(geoms), list(ys), list(fs))
         self.handle = C.c_void_p()
-        _check(_load().tnlm_batch_plan_create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
+        create = _load().tnlm_batch_plan_create_bf16 if bf16 else _load().tnlm_batch_plan_create
+        _check(create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
 
     def run(self, n_iterations: int, stream=None):
         _check(_load().tnlm_batch_plan_run(self.handle, int(n_iterations), _stream(stream)), "tnlm_batch_plan_run")

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "tnlm_internal.cuh"
@@ -370,60 +371,88 @@ namespace tnlm {
 
 // Validate one TNLM-R problem and allocate everything its iterations use, so
 // that an iteration issues only stream-ordered work (capturable).
-static tnlm_status prepare_reconstruct(tnlm_geometry *geo, const float *y, const float *f, const tnlm_params *p,
-                                       long long n_slots)
+static tnlm_status prepare_reconstruct(tnlm_geometry *geo, const void *y, const void *f, const tnlm_params *p,
+                                       long long n_slots, bool bf16 = false)
 {
     if (!geo || !y || !f) return arg_error("geometry, y and f must not be NULL");
     TNLM_TRY(check_params(p, true));
     const KGeom &kg = geo->kg;
     TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
+    if (bf16) {
+        if (p->p1_solver == 1) {
+            set_error("BF16 storage runs (P1) as gradient steps only (p1_solver = 0)");
+            return TNLM_ERR_NOT_IMPLEMENTED;
+        }
+        const bool box = (p->d == 1 || p->d == 2) && p->M >= 1 && p->M <= 3;
+        if (!box) {
+            set_error("BF16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", p->d, p->M);
+            return TNLM_ERR_NOT_IMPLEMENTED;
+        }
+    }
     TNLM_TRY(ensure_workspace(geo, p->gj_start == 1 || p->n_gj > 1, n_slots > 1 ? n_slots : 1));
     if (p->p1_solver == 1) TNLM_TRY(ensure_cgls_workspace(geo));
     prefix_workspace(geo);
     return TNLM_OK;
 }
 
+// The Eq. 8 sweep for each storage type.
+static tnlm_status sweep_t(const KGeom &kg, const float *wsrc, const float *vals, const float *g, float *out,
+                           const tnlm_params *p, int clip, cudaStream_t st)
+{
+    return launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, wsrc, vals, g, out, p->d, p->M, p->h, p->mu, clip, st);
+}
+
+static tnlm_status sweep_t(const KGeom &kg, const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g,
+                           uint16_t *out, const tnlm_params *p, int clip, cudaStream_t st)
+{
+    return launch_sweep_bf16(kg.nx, kg.ny, kg.nz, kg.np, wsrc, vals, g, out, p->d, p->M, p->h, p->mu, clip, st);
+}
+
 // One FBS iteration k of TNLM-R (Sec. 2.3) on stream st; timer may be null.
-static tnlm_status fbs_iteration(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, int k,
-                                 bool report, StageTimer *timer, cudaStream_t st)
+// T = float (FP32 storage) or uint16_t (BF16 storage: y, f, g and the sweep
+// scratch hold BF16; projections of the residual and every sum stay FP32).
+template <class T>
+static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, int k, bool report,
+                                 StageTimer *timer, cudaStream_t st)
 {
     const KGeom &kg = geo->kg;
     const long long nblk = forward_blocks(kg, geo->n_views_total);
+    T *g = reinterpret_cast<T *>(geo->d_g), *tmp = reinterpret_cast<T *>(geo->d_tmp);
     // step 1: (P1) from f^(k-1): CGLS (the paper's solver) or n_inner gradient steps
-    if (p->p1_solver == 1) {
-        if (timer) timer->begin(0);
-        TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
-        TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
-                                    report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
-                          st));
-        if (timer) timer->end();
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->p1_solver == 1) {
+            if (timer) timer->begin(0);
+            TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+            TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
+                                        report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
+                              st));
+            if (timer) timer->end();
+        }
     }
     for (int t = 0; t < (p->p1_solver == 1 ? 0 : p->n_inner); ++t) {
-        const float *src = t == 0 ? f : geo->d_g;
+        const T *src = t == 0 ? f : g;
         if (timer) timer->begin(0);
         TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
         if (timer) timer->end();
         if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
         if (timer) timer->begin(1);
-        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, geo->d_g, -p->tau, 1.0f, true,
+        TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, src, g, -p->tau, 1.0f, true,
                                     prefix_workspace(geo), geo->n_views_total, st));
         if (timer) timer->end();
     }
     // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
     if (timer) timer->begin(2);
     const int ngj = p->n_gj > 0 ? p->n_gj : 1;
-    const float *vals = p->gj_start ? f : geo->d_g;
+    const T *vals = p->gj_start ? f : g;
     for (int l = 0; l < ngj; ++l) {
         // sweeps alternate between f and the scratch image so that the last lands in f; with
         // gj_start = 1 the first sweep reads f and must write the scratch image
-        float *dst = ((ngj - 1 - l) % 2 == 0) ? f : geo->d_tmp;
-        if (dst == vals) dst = (vals == f) ? geo->d_tmp : f;  // never read and write one image
-        TNLM_TRY(launch_sweep(kg.nx, kg.ny, kg.nz, kg.np, geo->d_g, vals, geo->d_g, dst, p->d, p->M, p->h, p->mu,
-                              p->clip_nonneg && l == ngj - 1, st));
+        T *dst = ((ngj - 1 - l) % 2 == 0) ? f : tmp;
+        if (dst == vals) dst = (vals == f) ? tmp : f;  // never read and write one image
+        TNLM_TRY(sweep_t(kg, g, vals, g, dst, p, p->clip_nonneg && l == ngj - 1, st));
         vals = dst;
     }
-    if (vals != f)
-        TNLM_TRY_CUDA(cudaMemcpyAsync(f, vals, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+    if (vals != f) TNLM_TRY_CUDA(cudaMemcpyAsync(f, vals, sizeof(T) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
     if (timer) timer->end();
     return TNLM_OK;
 }
@@ -432,16 +461,19 @@ static tnlm_status fbs_iteration(tnlm_geometry *geo, const float *y, float *f, c
 
 extern "C" {
 
-tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, double *report,
-                             void *stream)
+}  // extern "C"
+
+template <class T>
+static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, double *report,
+                                 void *stream)
 {
     if (!p) return arg_error("params must not be NULL");
     const long long n_norms = (long long)p->n_outer * p->n_inner;
     const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
-    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots));
+    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots, std::is_same<T, uint16_t>::value));
     cudaStream_t st = as_stream(stream);
     StageTimer timer(geo, st);
-    for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration(geo, y, f, p, k, report != nullptr, &timer, st));
+    for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration<T>(geo, y, f, p, k, report != nullptr, &timer, st));
     if (report && n_norms > 0) {
         if (p->p1_solver == 1) {  // keep the residual before each of the n_inner CGLS iterations
             std::vector<double> tmp((size_t)n_slots);
@@ -457,22 +489,39 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
     return timer.finish();
 }
 
+extern "C" {
+
+tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const tnlm_params *p, double *report,
+                             void *stream)
+{
+    return reconstruct_t<float>(geo, y, f, p, report, stream);
+}
+
+tnlm_status tnlm_reconstruct_bf16(tnlm_geometry *geo, const uint16_t *y, uint16_t *f, const tnlm_params *p,
+                                  double *report, void *stream)
+{
+    return reconstruct_t<uint16_t>(geo, y, f, p, report, stream);
+}
+
 struct tnlm_batch_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
 
+}  // extern "C"
+
 // Validate and prepare every problem, then capture one FBS iteration of all of
 // them into *graph: the capture stream forks to up to 8 side streams (problem
 // b on side stream b mod 8) and joins back.
-static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+template <class T>
+static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const T *const *y, T *const *f,
                                  const tnlm_params *params, cudaGraph_t *graph)
 {
     if (n < 1 || !geoms || !y || !f || !params) return arg_error("need n >= 1 and non-NULL arrays");
     for (int b = 0; b < n; ++b) {
         for (int c = 0; c < b; ++c)
             if (geoms[c] == geoms[b]) return arg_error("a geometry handle may appear once per batch (it owns the workspace)");
-        TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1));
+        TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1, std::is_same<T, uint16_t>::value));
     }
     const int ns = n < 8 ? n : 8;  // parallel branches of the graph
     cudaStream_t cs = nullptr;
@@ -498,7 +547,7 @@ static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const float
         cuda_ok(cudaEventRecord(fork, cs), "cudaEventRecord");
         for (int s = 0; s < ns; ++s) cuda_ok(cudaStreamWaitEvent(side[s], fork, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < n && status == TNLM_OK; ++b) {
-            tnlm_status sb = fbs_iteration(geoms[b], y[b], f[b], &params[b], 0, false, nullptr, side[b % ns]);
+            tnlm_status sb = fbs_iteration<T>(geoms[b], y[b], f[b], &params[b], 0, false, nullptr, side[b % ns]);
             if (sb != TNLM_OK) status = sb;
         }
         for (int s = 0; s < ns; ++s) {
@@ -521,13 +570,14 @@ static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const float
     return status;
 }
 
-tnlm_status tnlm_batch_plan_create(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
-                                   const tnlm_params *params, tnlm_batch_plan **out)
+template <class T>
+static tnlm_status plan_create(int n, tnlm_geometry *const *geoms, const T *const *y, T *const *f,
+                               const tnlm_params *params, tnlm_batch_plan **out)
 {
     if (!out) return arg_error("out must not be NULL");
     *out = nullptr;
     cudaGraph_t graph = nullptr;
-    TNLM_TRY(capture_batch(n, geoms, y, f, params, &graph));
+    TNLM_TRY(capture_batch<T>(n, geoms, y, f, params, &graph));
     cudaGraphExec_t exec = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
@@ -546,6 +596,20 @@ tnlm_status tnlm_batch_plan_create(int n, tnlm_geometry *const *geoms, const flo
     plan->exec = exec;
     *out = plan;
     return TNLM_OK;
+}
+
+extern "C" {
+
+tnlm_status tnlm_batch_plan_create(int n, tnlm_geometry *const *geoms, const float *const *y, float *const *f,
+                                   const tnlm_params *params, tnlm_batch_plan **out)
+{
+    return plan_create<float>(n, geoms, y, f, params, out);
+}
+
+tnlm_status tnlm_batch_plan_create_bf16(int n, tnlm_geometry *const *geoms, const uint16_t *const *y,
+                                        uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out)
+{
+    return plan_create<uint16_t>(n, geoms, y, f, params, out);
 }
 
 tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream)

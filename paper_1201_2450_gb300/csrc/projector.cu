@@ -12,6 +12,8 @@
 // vector D (chord = delta_parameter * |D|) and anchor it near the voxels
 // (isocentre plane for the projector, the voxel column for the transpose)
 // so that FP32 positions keep ~1e-5 voxel resolution.
+#include <cuda_bf16.h>
+
 #include <cfloat>
 #include <cmath>
 
@@ -23,6 +25,15 @@ namespace {
 constexpr int kFwdBX = 32;                       // projector block: 32 u x BY v pixels (BY in {2, 4, 8})
 constexpr int kBpBX = 32, kBpBY = 4, kBpCH = 8;  // exact transpose block: 32 x 4 columns, 8 voxels in z each
 // band transpose: 32 x BY columns (BY in {2, 4}), CH z cells per thread (CH in {4, 8})
+
+// Storage of volumes and measured projections: FP32, or BF16 widened to FP32
+// on load (every sum stays FP32; a BF16 output is rounded once).
+__device__ __forceinline__ float ldg_v(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_v(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float ld_v(const float *p) { return *p; }
+__device__ __forceinline__ float ld_v(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_v(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_v(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 // Enter the slab 0 <= E + b G < n (voxel-index units) into [blo, bhi];
 // a ray parallel to the slab is inside iff 0 <= E < n (half-open cells).
@@ -88,10 +99,10 @@ __device__ __forceinline__ double block_sum_warps(double v, double *ws)
     return s;
 }
 
-template <int MODE, int BY>
+template <int MODE, int BY, class T>
 __global__ void __launch_bounds__(kFwdBX *BY)
-    k_forward(KGeom G, const ViewGeom *__restrict__ views, const float *__restrict__ vol,
-              const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials)
+    k_forward(KGeom G, const ViewGeom *__restrict__ views, const T *__restrict__ vol,
+              const T *__restrict__ y, float *__restrict__ out, double *__restrict__ partials)
 {
     __shared__ double ws[BY];
     const int iu = blockIdx.x * kFwdBX + threadIdx.x;
@@ -147,9 +158,9 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             float ba = ((float)(ia + pa) - Ea) * iva;
             float bb = Gb != 0.f ? ((float)(ib + pb) - Eb) * ivb : FLT_MAX;
             float bc = Gc != 0.f ? ((float)(ic + pc) - Ec) * ivc : FLT_MAX;
-            const float *__restrict__ fp = vol + (long long)V.phase * G.nvox;
+            const T *__restrict__ fp = vol + (long long)V.phase * G.nvox;
             int idx = ia * ta + ib * tb + ic * tc;
-            float fcur = __ldg(fp + idx);
+            float fcur = ldg_v(fp + idx);
             float bcur = blo;
             bool done = false;
             for (int it = 0; it <= na && !done; ++it) {
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                         bcur = bb;
                         ib += sb;
                         idx += sb * tb;
-                        fcur = (unsigned)ib < (unsigned)nb ? __ldg(fp + idx) : 0.f;
+                        fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
                         bb = ((float)(ib + pb) - Eb) * ivb;
                     }
                     acc = fmaf(fcur, fmaxf(bc - bcur, 0.f), acc);
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                         break;
                     }
                     idx += sc * tc;
-                    fcur = __ldg(fp + idx);
+                    fcur = ldg_v(fp + idx);
                     bc = ((float)(ic + pc) - Ec) * ivc;
                 }
                 if (done) break;
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                 if (hit) {
                     ib += sb;
                     idx += sb * tb;
-                    fcur = (unsigned)ib < (unsigned)nb ? __ldg(fp + idx) : 0.f;
+                    fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
                     bb = ((float)(ib + pb) - Eb) * ivb;
                 }
                 acc = fmaf(fcur, bend - e1, acc);
@@ -191,7 +202,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                 ia += sa;
                 if ((unsigned)ia >= (unsigned)na) break;
                 idx += sa * ta;
-                fcur = __ldg(fp + idx);
+                fcur = ldg_v(fp + idx);
                 ba = ((float)(ia + pa) - Ea) * iva;
             }
             acc *= len;
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
         if (MODE == 0) {
             out[o] = acc;
         } else {
-            const float r = acc - __ldg(y + o);
+            const float r = acc - ldg_v(y + o);
             out[o] = r * len;  // scaled residual consumed by the transpose
             r2 = (double)r * (double)r;
         }
@@ -212,10 +223,10 @@ __global__ void __launch_bounds__(kFwdBX *BY)
     }
 }
 
-template <bool SCALED>
+template <bool SCALED, class T>
 __global__ void __launch_bounds__(kBpBX *kBpBY)
     k_backproject(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
-                  const float *__restrict__ proj, const float *vin, float *vout, float alpha, float beta,
+                  const float *__restrict__ proj, const T *vin, T *vout, float alpha, float beta,
                   int nchunks)
 {
     constexpr int NT = kBpBX * kBpBY;
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
     for (int k = 0; k < nzc; ++k) {
         const long long o = base + (long long)k * G.nx * G.ny;
         const float bp = alpha * s_acc[k * NT + tid];
-        vout[o] = beta != 0.f ? fmaf(beta, vin[o], bp) : bp;
+        st_v(vout + o, beta != 0.f ? fmaf(beta, ld_v(vin + o), bp) : bp);
     }
 }
 
@@ -388,11 +399,11 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
 // and m; (ii) full rows between two bands, whose chord stays inside one cell:
 // they add r |D| dg each, summed with two prefix-sum loads.  Equal to the
 // per-cell exact tests of k_backproject up to rounding.
-template <bool SCALED, int CH, int BY>
+template <bool SCALED, int CH, int BY, class T>
 __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
     k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
-                        const float *__restrict__ proj, const float2 *__restrict__ pref, const float *vin,
-                        float *vout, float alpha, float beta, int nchunks)
+                        const float *__restrict__ proj, const float2 *__restrict__ pref, const T *vin,
+                        T *vout, float alpha, float beta, int nchunks)
 {
     constexpr int NT = kBpBX * BY;
     extern __shared__ float4 sm4[];
@@ -510,7 +521,7 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
         if (k < nzc) {
             const long long o = base + (long long)k * G.nx * G.ny;
             const float bp = alpha * acc[k];
-            vout[o] = beta != 0.f ? fmaf(beta, vin[o], bp) : bp;
+            st_v(vout + o, beta != 0.f ? fmaf(beta, ld_v(vin + o), bp) : bp);
         }
     }
 }
@@ -527,32 +538,47 @@ long long forward_blocks_max(const KGeom &kg, int n_views_total)
     return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + 1) / 2) * n_views_total;  // smallest BY = 2
 }
 
-template <int MODE, int BY>
-static void launch_forward_by(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
-                              const float *y, float *out, double *partials, cudaStream_t st)
+template <int MODE, int BY, class T>
+static void launch_forward_by(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol, const T *y,
+                              float *out, double *partials, cudaStream_t st)
 {
     dim3 grid((kg.nu + kFwdBX - 1) / kFwdBX, (kg.nv + BY - 1) / BY, n_views_total);
-    k_forward<MODE, BY><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views, vol, y, out, partials);
+    k_forward<MODE, BY, T><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views, vol, y, out, partials);
 }
 
-tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
-                           const float *y, float *out, double *partials, int mode, cudaStream_t st)
+template <class T>
+static tnlm_status launch_forward_t(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol,
+                                    const T *y, float *out, double *partials, int mode, cudaStream_t st)
 {
     if (kg.fwd_by != 2 && kg.fwd_by != 4 && kg.fwd_by != 8) {
         set_error("projector block rows must be 2, 4 or 8 (got %d)", kg.fwd_by);
         return TNLM_ERR_ARG;
     }
     if (mode == 0) {
-        if (kg.fwd_by == 2) launch_forward_by<0, 2>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
-        else if (kg.fwd_by == 4) launch_forward_by<0, 4>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
-        else launch_forward_by<0, 8>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+        if (kg.fwd_by == 2) launch_forward_by<0, 2, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+        else if (kg.fwd_by == 4) launch_forward_by<0, 4, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+        else launch_forward_by<0, 8, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
     } else {
-        if (kg.fwd_by == 2) launch_forward_by<1, 2>(kg, views, n_views_total, vol, y, out, partials, st);
-        else if (kg.fwd_by == 4) launch_forward_by<1, 4>(kg, views, n_views_total, vol, y, out, partials, st);
-        else launch_forward_by<1, 8>(kg, views, n_views_total, vol, y, out, partials, st);
+        if (kg.fwd_by == 2) launch_forward_by<1, 2, T>(kg, views, n_views_total, vol, y, out, partials, st);
+        else if (kg.fwd_by == 4) launch_forward_by<1, 4, T>(kg, views, n_views_total, vol, y, out, partials, st);
+        else launch_forward_by<1, 8, T>(kg, views, n_views_total, vol, y, out, partials, st);
     }
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
+}
+
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
+                           const float *y, float *out, double *partials, int mode, cudaStream_t st)
+{
+    return launch_forward_t<float>(kg, views, n_views_total, vol, y, out, partials, mode, st);
+}
+
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const uint16_t *vol,
+                           const uint16_t *y, float *out, double *partials, int mode, cudaStream_t st)
+{
+    using B = __nv_bfloat16;
+    return launch_forward_t<B>(kg, views, n_views_total, reinterpret_cast<const B *>(vol),
+                               reinterpret_cast<const B *>(y), out, partials, mode, st);
 }
 
 bool bands_apply(const KGeom &kg)
@@ -570,26 +596,26 @@ size_t prefix_floats(const KGeom &kg, int n_views_total)
     return (size_t)2 * n_views_total * (kg.nv + 1) * kg.nu + (size_t)n_views_total * kg.npix;
 }
 
-template <int CH, int BY>
+template <int CH, int BY, class T>
 static tnlm_status launch_bands(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *src,
-                                const float2 *pref, const float *vin, float *vout, float alpha, float beta,
-                                cudaStream_t st)
+                                const float2 *pref, const T *vin, T *vout, float alpha, float beta, cudaStream_t st)
 {
     const int nchb = (kg.nz + CH - 1) / CH;
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + BY - 1) / BY, kg.np * nchb);
     const size_t smem = sizeof(float4) * kg.nv;
     if (smem > 48 * 1024)
-        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CH, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-    k_backproject_bands<true, CH, BY><<<grid, dim3(kBpBX, BY), smem, st>>>(kg, views, view_off, src, pref, vin, vout,
-                                                                            alpha, beta, nchb);
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CH, BY, T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_backproject_bands<true, CH, BY, T><<<grid, dim3(kBpBX, BY), smem, st>>>(kg, views, view_off, src, pref, vin, vout,
+                                                                               alpha, beta, nchb);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
 }
 
-tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
-                               const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
-                               int n_views_total, cudaStream_t st)
+template <class T>
+static tnlm_status launch_backproject_t(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                                        const T *vin, T *vout, float alpha, float beta, bool scaled, float *pref_ws,
+                                        int n_views_total, cudaStream_t st)
 {
     const int nchunks = (kg.nz + kBpCH - 1) / kBpCH;
     dim3 block(kBpBX, kBpBY);
@@ -605,13 +631,13 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
         TNLM_TRY_CUDA(cudaGetLastError());
         const float *src = scaled ? proj : rtil;
         if (kg.bp_ch == 8 && kg.bp_by == 4)
-            TNLM_TRY((launch_bands<8, 4>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+            TNLM_TRY((launch_bands<8, 4, T>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
         else if (kg.bp_ch == 8 && kg.bp_by == 2)
-            TNLM_TRY((launch_bands<8, 2>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+            TNLM_TRY((launch_bands<8, 2, T>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
         else if (kg.bp_ch == 4 && kg.bp_by == 4)
-            TNLM_TRY((launch_bands<4, 4>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+            TNLM_TRY((launch_bands<4, 4, T>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
         else if (kg.bp_ch == 4 && kg.bp_by == 2)
-            TNLM_TRY((launch_bands<4, 2>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
+            TNLM_TRY((launch_bands<4, 2, T>(kg, views, view_off, src, pref, vin, vout, alpha, beta, st)));
         else {
             set_error("band transpose shape must be CH in {4, 8} and BY in {2, 4} (got %d, %d)", kg.bp_ch, kg.bp_by);
             return TNLM_ERR_ARG;
@@ -620,15 +646,32 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
     }
     const size_t smem = sizeof(float4) * kg.nv + sizeof(float) * kBpCH * kBpBX * kBpBY;
     if (smem > 48 * 1024) {
-        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if (scaled)
-        k_backproject<true><<<grid, block, smem, st>>>(kg, views, view_off, proj, vin, vout, alpha, beta, nchunks);
+        k_backproject<true, T><<<grid, block, smem, st>>>(kg, views, view_off, proj, vin, vout, alpha, beta, nchunks);
     else
-        k_backproject<false><<<grid, block, smem, st>>>(kg, views, view_off, proj, vin, vout, alpha, beta, nchunks);
+        k_backproject<false, T><<<grid, block, smem, st>>>(kg, views, view_off, proj, vin, vout, alpha, beta, nchunks);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
+}
+
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
+                               int n_views_total, cudaStream_t st)
+{
+    return launch_backproject_t<float>(kg, views, view_off, proj, vin, vout, alpha, beta, scaled, pref_ws,
+                                       n_views_total, st);
+}
+
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const uint16_t *vin, uint16_t *vout, float alpha, float beta, bool scaled,
+                               float *pref_ws, int n_views_total, cudaStream_t st)
+{
+    using B = __nv_bfloat16;
+    return launch_backproject_t<B>(kg, views, view_off, proj, reinterpret_cast<const B *>(vin),
+                                   reinterpret_cast<B *>(vout), alpha, beta, scaled, pref_ws, n_views_total, st);
 }
 
 }  // namespace tnlm

@@ -60,6 +60,9 @@ void set_error(const char *fmt, ...);
 // partial sums of (P vol - y)^2 in partials[forward_blocks(g)].
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const float *vol,
                            const float *y, float *out, double *partials, int mode, cudaStream_t st);
+// BF16 storage of vol and y (bit patterns), FP32 arithmetic and FP32 output
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const uint16_t *vol,
+                           const uint16_t *y, float *out, double *partials, int mode, cudaStream_t st);
 long long forward_blocks(const KGeom &kg, int n_views_total);
 long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
 
@@ -70,6 +73,10 @@ long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
                                const float *vin, float *vout, float alpha, float beta, bool scaled, float *pref_ws,
                                int n_views_total, cudaStream_t st);
+// BF16 storage of vin / vout (bit patterns); proj stays FP32
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const uint16_t *vin, uint16_t *vout, float alpha, float beta, bool scaled,
+                               float *pref_ws, int n_views_total, cudaStream_t st);
 bool bands_apply(const KGeom &kg);
 size_t prefix_floats(const KGeom &kg, int n_views_total);
 

@@ -596,3 +596,59 @@ def test_reconstruct_batch_graph_equals_single_calls():
     torch.cuda.synchronize()
     for a, b in zip(single, fp):
         assert torch.equal(a, b)
+
+
+def _bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).bfloat16().float().numpy()
+
+
+@pytest.mark.parametrize("cfg, n_outer", [(synth.C1, synth.C1.n_outer), (C2_TINY, 10)])
+def test_reconstruct_bf16_error_vs_fp64(ora, cfg, n_outer):
+    """TNLM-R with BF16 storage against the FP64 oracle on the same
+    (BF16-representable) measurements.  Each iteration rounds g and f to BF16
+    once (unit roundoff u = 2^-9 each) and the gradient step with tau <= 1/L
+    and the averaging sweep do not amplify earlier errors much, so the error
+    stays within 2 n_outer u; the measured value is far below that bound."""
+    pb = synth.recon_problem(cfg)
+    OG = ora.Geometry(pb.geom)
+    L = ora.power_norm(OG, synth.uniform(OG.vol_shape, 7), 30)
+    tau = float(np.float32(1.0 / L))
+    y = _bf16_round(pb.y.numpy())
+    f_ref, rep_ref = ora.reconstruct(OG, y, np.zeros(OG.vol_shape), tau, cfg.d, cfg.M, cfg.h, cfg.mu, n_outer,
+                                     with_report=True)
+    G = tnlm.Geometry(pb.geom)
+    p = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=n_outer)
+    f16 = torch.zeros(G.vol_shape, device="cuda", dtype=torch.bfloat16)
+    _, rep = tnlm.tnlm_reconstruct_bf16(G, cuda(y).bfloat16(), f16, p, report=True)
+    f32 = torch.zeros(G.vol_shape, device="cuda")
+    tnlm.tnlm_reconstruct(G, cuda(y), f32, p)
+    err16 = rel_l2(f16.float().cpu().numpy(), f_ref)
+    err32 = rel_l2(f32.cpu().numpy(), f_ref)
+    print(f"BF16 storage rel-L2 vs FP64 after {n_outer} iterations: {err16:.3e} (FP32: {err32:.1e})")
+    assert err32 <= RTOL
+    assert err16 <= 2 * n_outer * BF16_U
+    np.testing.assert_allclose(rep, rep_ref, rtol=4 * n_outer * BF16_U)
+    assert torch.all(f16.float() >= 0)
+
+
+def test_batch_plan_bf16_equals_single_calls():
+    """BF16 problems in one captured plan equal separate BF16 calls bit for bit."""
+    geoms = [GEOMS["ragged_uneven"], synth.C1.geometry()]
+    params = [tnlm.Params(d=1, M=2, h=0.02, mu=0.8, tau=1e-4, n_outer=2),
+              tnlm.Params(d=2, M=1, h=0.03, mu=1.1, tau=5e-5, n_outer=2, n_gj=2, gj_start=1)]
+    Gs = [tnlm.Geometry(g) for g in geoms]
+    ys = [cuda(synth.uniform(G.proj_shape, 270 + k) * 0.3).bfloat16() for k, G in enumerate(Gs)]
+    f0 = [cuda(synth.smooth_volume(G.vol_shape, 280 + k)).bfloat16() for k, G in enumerate(Gs)]
+    single = []
+    for G, y, f, p in zip(Gs, ys, f0, params):
+        x = f.clone()
+        tnlm.tnlm_reconstruct_bf16(G, y, x, p)
+        single.append(x)
+    Gb = [tnlm.Geometry(g) for g in geoms]
+    fb = [f.clone() for f in f0]
+    plan = tnlm.BatchPlan(Gb, ys, fb, params)
+    plan.run(2)
+    plan.close()
+    torch.cuda.synchronize()
+    for a, b in zip(single, fb):
+        assert torch.equal(a, b)
