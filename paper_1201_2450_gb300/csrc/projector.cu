@@ -484,12 +484,16 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
                     blo_n = __float2int_ru(fmaxf(fminf(pa, pb) - 1e-3f, -1.f));
                     bhi_n = __float2int_rd(fminf(fmaxf(pa, pb) + 1e-3f, (float)G.nv));
                 }
-                // band rows of boundary m: split the chord at the crossing of z = zm
+                // band rows of boundary m: split the chord at the crossing of z = zm.  A band is
+                // usually narrower than one detector row, so its first row is handled without a
+                // loop (predicated: the loads of all boundaries can be issued together) and any
+                // further rows by the loop after it.
                 const int r0 = max(0, blo_m), r1 = min(G.nv - 1, bhi_m);
-                for (int iv = r0; iv <= r1; ++iv) {
+                auto band_row = [&](int iv, bool on) {
                     const float4 rw = s_row[iv];
                     float r = __ldg(pc + iv * G.nu);
                     if (!SCALED) r *= sqrtf(len_u2 + rw.z);
+                    r = on ? r : 0.f;  // a row outside the band adds nothing
                     float below;  // part of the chord below z = zm
                     if (rw.x != 0.f) {
                         const float gs = fmaf(-ac, rw.x, zm) * rw.y;  // crossing parameter (column-relative)
@@ -499,7 +503,9 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
                     }
                     if (m > 0) acc[m - 1] = fmaf(r, below, acc[m - 1]);
                     if (m < nzc) acc[m] = fmaf(r, dg - below, acc[m]);
-                }
+                };
+                band_row(r0 <= r1 ? r0 : 0, r0 <= r1);
+                for (int iv = r0 + 1; iv <= r1; ++iv) band_row(iv, true);
                 // full rows of cell m: strictly between the bands of boundaries m and m+1
                 if (m < nzc) {
                     const int f0 = max(0, bhi_m + 1), f1 = min(G.nv - 1, blo_n - 1);
