@@ -508,12 +508,12 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
                 for (int iv = r0 + 1; iv <= r1; ++iv) band_row(iv, true);
                 // full rows of cell m: strictly between the bands of boundaries m and m+1
                 if (m < nzc) {
+                    // predicated as well: an empty range reads one prefix entry twice and adds 0
                     const int f0 = max(0, bhi_m + 1), f1 = min(G.nv - 1, blo_n - 1);
-                    if (f0 <= f1) {
-                        const float2 e0 = __ldg(pp + (long long)f0 * G.nu);
-                        const float2 e1 = __ldg(pp + (long long)(f1 + 1) * G.nu);
-                        acc[m] = fmaf((e1.x - e0.x) + (e1.y - e0.y), dg, acc[m]);
-                    }
+                    const bool hasf = f0 <= f1;
+                    const float2 e0 = __ldg(pp + (long long)(hasf ? f0 : 0) * G.nu);
+                    const float2 e1 = __ldg(pp + (long long)(hasf ? f1 + 1 : 0) * G.nu);
+                    acc[m] = fmaf((e1.x - e0.x) + (e1.y - e0.y), dg, acc[m]);
                 }
                 zm = zn;
                 blo_m = blo_n;
