@@ -154,56 +154,69 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             int ib = clamp_floor(fmaf(blo, Gb, Eb), nb);
             int ic = clamp_floor(fmaf(blo, Gc, Ec), nc);
             // next plane crossing on each axis, in the same form as the entry/exit test above so
-            // that exit planes compare equal to bhi
-            float ba = ((float)(ia + pa) - Ea) * iva;
-            float bb = Gb != 0.f ? ((float)(ib + pb) - Eb) * ivb : FLT_MAX;
-            float bc = Gc != 0.f ? ((float)(ic + pc) - Ec) * ivc : FLT_MAX;
+            // that exit planes compare equal to bhi; the plane coordinates are kept as exact float
+            // shadows of the integer indices (small integers), so no conversion per step
+            float fa = (float)(ia + pa), fb = (float)(ib + pb), fc = (float)(ic + pc);
+            const float saf = (float)sa, sbf = (float)sb, scf = (float)sc;
+            float ba = (fa - Ea) * iva;
+            float bb = Gb != 0.f ? (fb - Eb) * ivb : FLT_MAX;
+            float bc = Gc != 0.f ? (fc - Ec) * ivc : FLT_MAX;
+            // a-slabs visited: from the entry cell to the cell holding the exit point (a slab of zero
+            // length at either end is harmless; every index stays inside the volume)
+            const int ia_last = clamp_floor(fmaf(bhi, Ga, Ea), na);
+            const int n_slabs = max(1, sa > 0 ? ia_last - ia + 1 : ia - ia_last + 1);
             const T *__restrict__ fp = vol + (long long)V.phase * G.nvox;
             int idx = ia * ta + ib * tb + ic * tc;
             float fcur = ldg_v(fp + idx);
             float bcur = blo;
-            bool done = false;
-            for (int it = 0; it <= na && !done; ++it) {
+            for (int k = 0; k < n_slabs; ++k) {
                 const float bend = fminf(ba, bhi);  // end of this a-slab inside the volume
-                for (int rc = 0; rc < 4 && bc < bend; ++rc) {  // c crossings (coherent, rare)
-                    if (bb < bc) {
-                        acc = fmaf(fcur, fmaxf(bb - bcur, 0.f), acc);
-                        bcur = bb;
-                        ib += sb;
-                        idx += sb * tb;
-                        fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
-                        bb = ((float)(ib + pb) - Eb) * ivb;
+                if (bc < bend) {                    // c crossings (coherent across the warp, rare)
+                    bool out = false;
+                    for (int rc = 0; rc < 4 && bc < bend; ++rc) {
+                        if (bb < bc) {
+                            acc = fmaf(fcur, bb - bcur, acc);
+                            bcur = bb;
+                            ib += sb;
+                            idx += sb * tb;
+                            fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
+                            fb += sbf;
+                            bb = (fb - Eb) * ivb;
+                        }
+                        acc = fmaf(fcur, bc - bcur, acc);
+                        bcur = bc;
+                        ic += sc;
+                        if ((unsigned)ic >= (unsigned)nc || (unsigned)ib >= (unsigned)nb) {
+                            out = true;
+                            break;
+                        }
+                        idx += sc * tc;
+                        fcur = ldg_v(fp + idx);
+                        fc += scf;
+                        bc = (fc - Ec) * ivc;
                     }
-                    acc = fmaf(fcur, fmaxf(bc - bcur, 0.f), acc);
-                    bcur = bc;
-                    ic += sc;
-                    if ((unsigned)ic >= (unsigned)nc || (unsigned)ib >= (unsigned)nb) {
-                        done = true;
-                        break;
-                    }
-                    idx += sc * tc;
-                    fcur = ldg_v(fp + idx);
-                    bc = ((float)(ic + pc) - Ec) * ivc;
+                    if (out) break;
                 }
-                if (done) break;
                 // at most one b crossing in the rest of the slab
                 const bool hit = bb < bend;
                 const float e1 = hit ? bb : bend;
-                acc = fmaf(fcur, fmaxf(e1 - bcur, 0.f), acc);
+                acc = fmaf(fcur, e1 - bcur, acc);
                 if (hit) {
                     ib += sb;
                     idx += sb * tb;
                     fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
-                    bb = ((float)(ib + pb) - Eb) * ivb;
+                    fb += sbf;
+                    bb = (fb - Eb) * ivb;
                 }
                 acc = fmaf(fcur, bend - e1, acc);
                 bcur = bend;
-                if (bend >= bhi || (unsigned)ib >= (unsigned)nb) break;
-                ia += sa;
-                if ((unsigned)ia >= (unsigned)na) break;
-                idx += sa * ta;
-                fcur = ldg_v(fp + idx);
-                ba = ((float)(ia + pa) - Ea) * iva;
+                if (k + 1 < n_slabs) {
+                    ia += sa;
+                    idx += sa * ta;
+                    fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
+                    fa += saf;
+                    ba = (fa - Ea) * iva;
+                }
             }
             acc *= len;
         }
