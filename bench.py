@@ -48,10 +48,10 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
     # the transpose stage is the column scan plus the band kernel
-    "k_forward": {"bytes_per_launch": int((271.703552e6 + 147.8272e6) * 10 / 6), "source_sha": "d98d64215d275221"},
-    "k_backproject": {"bytes_per_launch": int((169.89824e6 + 285.024512e6 + 557.616896e6 + 93.241856e6) * 10 / 6),
-                      "source_sha": "d98d64215d275221"},
-    "k_sweep": {"bytes_per_launch": int((161.970944e6 + 83.84768e6) * 10 / 6), "source_sha": "4e8b41aeca19e017"},
+    "k_forward": {"bytes_per_launch": int((273.490432e6 + 147.899392e6) * 10 / 6), "source_sha": "c76a4c3629b9ff59"},
+    "k_backproject": {"bytes_per_launch": int((169.964544e6 + 285.275136e6 + 557.31456e6 + 93.097984e6) * 10 / 6),
+                      "source_sha": "c76a4c3629b9ff59"},
+    "k_sweep": {"bytes_per_launch": int((162.90304e6 + 84.224256e6) * 10 / 6), "source_sha": "4e8b41aeca19e017"},
 }
 
 

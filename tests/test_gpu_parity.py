@@ -72,6 +72,20 @@ def test_backproject_matches_oracle(ora, name):
     assert rel_l2(bt, ora.backproject(OG, y)) <= RTOL
 
 
+def test_tall_detector_pair_matches_oracle(ora):
+    """A 4096-row detector: the per-row table of the transpose (16 B per row)
+    needs more than the default 48 KB of shared memory; projector and
+    transpose still match the oracle."""
+    geom = synth.make_geometry(nx=12, ny=11, nz=10, dx=1.0, nu=16, nv=4096, du=1.0, dv=0.01, sad=300.0, sdd=450.0,
+                               n_phases=2, views_per_phase=[3, 4], angle_offset=0.2)
+    G = tnlm.Geometry(geom)
+    OG = ora.Geometry(geom)
+    x = synth.uniform(G.vol_shape, 104)
+    assert rel_l2(tnlm.tnlm_project(G, cuda(x)).cpu().numpy(), ora.project(OG, x)) <= RTOL
+    y = synth.uniform(G.proj_shape, 105)
+    assert rel_l2(tnlm.tnlm_backproject(G, cuda(y)).cpu().numpy(), ora.backproject(OG, y)) <= RTOL
+
+
 @pytest.mark.parametrize("name", list(GEOMS))
 def test_adjoint_identity_gpu_pair(name):
     G = tnlm.Geometry(GEOMS[name])
