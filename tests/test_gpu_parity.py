@@ -354,6 +354,52 @@ def test_full_size_sweep_sampled_voxels(ora, c2_full):
     assert rel_l2(got, ref) <= RTOL
 
 
+@pytest.fixture(scope="module")
+def c3_full():
+    g, _ = synth.enhance_input(synth.C3, device="cuda")
+    return g.contiguous()
+
+
+def _crop(a, lo, hi):
+    """a[:, z0:z1, y0:y1, x0:x1] for lo = (z0, y0, x0), hi = (z1, y1, x1), clipped to the volume."""
+    _, nz, ny, nx = a.shape
+    z0, y0, x0 = max(lo[0], 0), max(lo[1], 0), max(lo[2], 0)
+    z1, y1, x1 = min(hi[0], nz), min(hi[1], ny), min(hi[2], nx)
+    return a[:, z0:z1, y0:y1, x0:x1], (z0, y0, x0)
+
+
+def test_full_size_enhance_sampled_voxels_and_crop(ora, c3_full):
+    """TNLM-E at the full enhancement size (10 x 512^2 x 128, d = 2, M = 3).
+    One sweep: 200 sampled voxels, each evaluated by the oracle on a crop of
+    radius M + d around it (exact: every patch read and window candidate of
+    the voxel lies in the crop, and where the crop meets the volume edge the
+    clamping is the volume's).  Two sweeps: an interior 8^3 block (all 10
+    phases) against the oracle's two sweeps on that block plus a halo of
+    2 (M + d) = 10 voxels, the dependency radius of two sweeps."""
+    cfg = synth.C3
+    d, M, h, mu = cfg.d, cfg.M, cfg.h, cfg.mu
+    g = c3_full
+    f1 = tnlm.tnlm_enhance(g, tnlm.Params(d=d, M=M, h=h, mu=mu, n_outer=1, clip_nonneg=0)).cpu()
+    gc = g.cpu()
+    _, nz, ny, nx = g.shape
+    r = M + d
+    rng = np.random.default_rng(175)
+    got, ref = [], []
+    for _ in range(200):
+        ph, z, y, x = (int(rng.integers(10)), int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx)))
+        c, (z0, y0, x0) = _crop(gc, (z - r, y - r, x - r), (z + r + 1, y + r + 1, x + r + 1))
+        c = c.numpy().astype(np.float64)
+        ref.append(ora.gj_voxel(c, c, c, ph, x - x0, y - y0, z - z0, d, M, h, mu, 0))
+        got.append(float(f1[ph, z, y, x]))
+    assert rel_l2(np.array(got), np.array(ref)) <= RTOL
+    f2 = tnlm.tnlm_enhance(g, tnlm.Params(d=d, M=M, h=h, mu=mu, n_outer=2, clip_nonneg=0)).cpu()
+    hw, lo = 2 * r, (60, 250, 250)
+    c, _ = _crop(gc, (lo[0] - hw, lo[1] - hw, lo[2] - hw), (lo[0] + 8 + hw, lo[1] + 8 + hw, lo[2] + 8 + hw))
+    e2 = ora.enhance(c.numpy(), d, M, h, mu, 2)[:, hw:hw + 8, hw:hw + 8, hw:hw + 8]
+    got2 = f2[:, lo[0]:lo[0] + 8, lo[1]:lo[1] + 8, lo[2]:lo[2] + 8].numpy()
+    assert rel_l2(got2, e2) <= RTOL
+
+
 def test_full_size_fused_iteration_equals_composed_calls(c2_full):
     """One tnlm_reconstruct iteration in the benchmark's launch configuration
     (fused residual, scaled transpose, sweep with positivity) equals the same
