@@ -338,6 +338,8 @@ def run_ours(args, rank, world, local):
                    "launch_shapes": shapes if shapes else "defaults (projector rows 4, transpose 8 cells x 4 rows, "
                                                          "sweep shape 0)"},
         "tnlm_voxel_updates_per_s": round(nvox_upd / sweep_s, 1),
+        "projector_segments_per_s": round(nnz / (per_launch_ms["k_forward"] / 1e3), 1),
+        "transpose_segments_per_s": round(nnz / (per_launch_ms["k_backproject"] / 1e3), 1),
         "tnlm_pair_evals_per_s": round(sweep_pairs(cfg) / sweep_s, 1),
         "stage_ms_per_launch": {n: round(per_launch_ms[n], 4) for n in names},
         "hbm": hbm,
@@ -547,15 +549,15 @@ def measure_batch(tnlm, synth, stream, n_outer: int = 3) -> dict:
 def cpu_baseline_sample(cfg, pb=None) -> dict:
     """Time the FP64 oracle as it stands on a bounded sample of one FBS
     iteration of the workload and extrapolate to iterations/s:
-    projection and transpose of 8 views (x 360 views), one sweep on a
-    3-phase 256 x 256 x 8 slab (x voxel-updates of 10 x 256^2 x 64)."""
+    projection and transpose of 12 views (x 360 views), one sweep on a
+    3-phase 256 x 256 x 12 slab (x voxel-updates of 10 x 256^2 x 64)."""
     import oracle
     from paper_1201_2450_gb300 import synth
 
     oracle.build()
     geom = cfg.geometry() if pb is None else pb.geom
     truth = (pb.truth.cpu() if pb is not None else synth.rasterize(geom, synth._objects(cfg))).numpy()
-    nview = 8
+    nview, nsl = 12, 12
     sub = dict(geom)
     sub["nviews"] = np.array([nview], np.int32)
     sub["angles"] = np.asarray(geom["angles"][:nview])
@@ -566,15 +568,15 @@ def cpu_baseline_sample(cfg, pb=None) -> dict:
     t1 = time.perf_counter()
     oracle.backproject(G1, p)
     t2 = time.perf_counter()
-    slab = truth[:3, 28:36].astype(np.float64)
+    slab = truth[:3, 26:26 + nsl].astype(np.float64)
     oracle.gj_sweep(slab, slab, slab, cfg.d, cfg.M, cfg.h, cfg.mu, 1)
     t3 = time.perf_counter()
     n_views = int(np.sum(geom["nviews"]))
     per_iter = (t1 - t0) / nview * n_views + (t2 - t1) / nview * n_views + \
-        (t3 - t2) * (cfg.n_phases * cfg.vol[2]) / (3 * 8)
+        (t3 - t2) * (cfg.n_phases * cfg.vol[2]) / (3 * nsl)
     return {"value": round(1.0 / per_iter, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle: P and P^T of {nview} views (x{n_views}), one sweep on 3 phases x 256x256x8 "
-                      f"(x{cfg.n_phases * cfg.vol[2] / 24:.1f}); {t3 - t0:.1f} s measured, "
+            "sample": f"FP64 oracle: P and P^T of {nview} views (x{n_views / nview:.0f}), one sweep on 3 phases x "
+                      f"256x256x{nsl} (x{cfg.n_phases * cfg.vol[2] / (3 * nsl):.1f}); {t3 - t0:.1f} s measured, "
                       f"{per_iter:.1f} s per iteration extrapolated"}
 
 
