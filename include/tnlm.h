@@ -9,6 +9,8 @@
  *  - Volumes are float32 [n_phases][nz][ny][nx] (x fastest), contiguous.
  *  - Projections are float32 [sum of n_views][nv][nu] (u fastest),
  *    contiguous; the views of phase 0 come first, then phase 1, ...
+ *  - The *_bf16 calls take the same layouts as bfloat16 bit patterns
+ *    (uint16_t); they compute in FP32 and round each output once.
  *  - Every array argument is a DEVICE pointer owned by the caller, on the
  *    device that was current when the geometry was created (or, for the
  *    geometry-free calls, the current device).  The library never frees it.
@@ -107,7 +109,11 @@ tnlm_status tnlm_project(const tnlm_geometry *geom, const float *vol, float *pro
 /* vol = beta * vol + alpha * P^T proj: the exact transpose of tnlm_project,
  * evaluated voxel-driven (each voxel gathers over the pixels whose rays cross
  * it), as used by the (P1) gradient of Eq. 5.  vol may hold garbage when
- * beta == 0. */
+ * beta == 0.  Uses the handle's column prefix-sum workspace (cudaMalloc on
+ * first use, 2 sum(n_views) (nv+1) nu + sum(n_views) nu nv floats; if that
+ * allocation fails, or very thin slices make it inapplicable, the exact
+ * per-cell form runs instead with the same results up to rounding), so calls
+ * on one handle must not overlap on the GPU. */
 tnlm_status tnlm_backproject(const tnlm_geometry *geom, const float *proj, float *vol, float alpha, float beta,
                              void *stream);
 
@@ -285,7 +291,9 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * tnlm_autotune_sweep does the same for the sweep alone (bf16 != 0: the BF16
  * storage kernels), writing the chosen shape to *shape (nullable).
  * tnlm_set_launch_shapes / tnlm_set_sweep_shape set a shape directly
- * (TNLM_ERR_ARG for a shape that is not compiled). */
+ * (TNLM_ERR_ARG for a shape that is not compiled).  The sweep-shape table
+ * is shared by the whole process: change it from one host thread at a time
+ * and not while sweeps are being enqueued from another thread. */
 tnlm_status tnlm_autotune(tnlm_geometry *geom, const tnlm_params *params, int *choice, void *stream);
 tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int n_phases, int d, int M, float h, int bf16, int *shape,
                                 void *stream);
