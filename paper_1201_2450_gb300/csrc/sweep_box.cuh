@@ -206,19 +206,21 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
                         if (!(vxy0 && vz)) a.x = -FLT_MAX;
                         if (!(vxy1 && vz)) a.y = -FLT_MAX;
                     }
-                    if (a.x > kRescale) {  // candidate beats the reference by 2^kRescale: move it
-                        const float sc = ex2(-a.x);
-                        N[k].x *= sc;
-                        Z[k].x *= sc;
-                        mref[k].x = Dv.x * c2;
-                        a.x = 0.f;
-                    }
-                    if (a.y > kRescale) {
-                        const float sc = ex2(-a.y);
-                        N[k].y *= sc;
-                        Z[k].y *= sc;
-                        mref[k].y = Dv.y * c2;
-                        a.y = 0.f;
+                    if (fmaxf(a.x, a.y) > kRescale) {  // rare: one test for both outputs of the pair
+                        if (a.x > kRescale) {  // candidate beats the reference by 2^kRescale: move it
+                            const float sc = ex2(-a.x);
+                            N[k].x *= sc;
+                            Z[k].x *= sc;
+                            mref[k].x = Dv.x * c2;
+                            a.x = 0.f;
+                        }
+                        if (a.y > kRescale) {
+                            const float sc = ex2(-a.y);
+                            N[k].y *= sc;
+                            Z[k].y *= sc;
+                            mref[k].y = Dv.y * c2;
+                            a.y = 0.f;
+                        }
                     }
                     const float2 e = make_float2(ex2(a.x), ex2(a.y));
                     N[k] = __ffma2_rn(e, vw[q + k], N[k]);
