@@ -436,6 +436,10 @@ def measure_variants(tnlm, synth, geom, y, stream, params) -> dict:
     out["energy_grad_workload"] = "E(f) and grad E, 10 x 128^3 at 2 mm, 40 views x 256x192, patch 3^3, window 5^3"
     out["energy_grad_ms"] = round(_time_ms(lambda: tnlm.tnlm_energy_grad(g4, pb4.y, f4, pb4.truth, p4, grad=grad4),
                                            stream), 3)
+    y16, f16, a16 = pb4.y.bfloat16(), f4.bfloat16(), pb4.truth.bfloat16()
+    out["energy_grad_bf16_ms"] = round(_time_ms(lambda: tnlm.tnlm_energy_grad_bf16(g4, y16, f16, a16, p4, grad=grad4),
+                                                stream), 3)
+    del y16, f16, a16
     ga4 = torch.empty_like(f4)
     out["energy_grad_weights_ms"] = round(_time_ms(
         lambda: tnlm.tnlm_energy_grad_weights(f4, pb4.truth, c4.d, c4.M, c4.h, grad_a=ga4), stream), 3)

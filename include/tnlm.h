@@ -256,6 +256,13 @@ tnlm_status tnlm_cgls(tnlm_geometry *geom, const float *y, float *x, int n_iter,
 tnlm_status tnlm_energy_grad(tnlm_geometry *geom, const float *y, const float *f, const float *a,
                              const tnlm_params *params, double *energy, float *grad, void *stream);
 
+/* tnlm_energy_grad with y, f and a stored as bfloat16 bit patterns (the
+ * gradient stays FP32): every value is widened to FP32 when read, so the
+ * result equals tnlm_energy_grad on the widened inputs.  d in {1,2}, M in
+ * {1,2,3} (TNLM_ERR_NOT_IMPLEMENTED otherwise). */
+tnlm_status tnlm_energy_grad_bf16(tnlm_geometry *geom, const uint16_t *y, const uint16_t *f, const uint16_t *a,
+                                  const tnlm_params *params, double *energy, float *grad, void *stream);
+
 /* Gradient of the TNLM half of the energy, 1/2 sum_i J[f_i, f_{i+1}] (J of
  * Eq. 2 over the search window, direction-0 weights of Eq. 9 computed from
  * a), with respect to the weight-source images a, f held fixed: the

@@ -28,7 +28,7 @@ __all__ = [
     "build", "TnlmError", "Params", "Geometry", "tnlm_create_geometry", "tnlm_project", "tnlm_backproject",
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
-    "tnlm_energy_grad", "tnlm_energy_grad_weights", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
+    "tnlm_energy_grad", "tnlm_energy_grad_weights", "tnlm_energy_grad_bf16", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path",
 ]
@@ -118,6 +118,7 @@ def _load():
             "tnlm_gauss_jacobi_bf16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_energy_grad": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
             "tnlm_energy_grad_weights": (i, [i, i, i, i, vp, vp, i, i, f, vp, vp]),
+            "tnlm_energy_grad_bf16": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
             "tnlm_reconstruct_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params), vp]),
             "tnlm_batch_plan_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
                                            C.POINTER(vp)]),
@@ -452,6 +453,22 @@ def tnlm_energy_grad(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: torch.
                                     _dev(f, "f", geom.device, geom.vol_shape), _dev(a, "a", geom.device, geom.vol_shape),
                                     C.byref(p), C.byref(E), _dev(grad, "grad", geom.device, geom.vol_shape),
                                     _stream(stream)), "tnlm_energy_grad")
+    return E.value, grad
+
+
+def tnlm_energy_grad_bf16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: torch.Tensor, params: Params,
+                          grad: torch.Tensor | None = None, stream=None):
+    """tnlm_energy_grad on bfloat16 y, f and a; the gradient is FP32."""
+    if grad is None:
+        grad = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+    E = C.c_double()
+    p = params._c()
+    b = torch.bfloat16
+    _check(_load().tnlm_energy_grad_bf16(geom.handle, _dev(y, "y", geom.device, geom.proj_shape, b),
+                                         _dev(f, "f", geom.device, geom.vol_shape, b),
+                                         _dev(a, "a", geom.device, geom.vol_shape, b), C.byref(p), C.byref(E),
+                                         _dev(grad, "grad", geom.device, geom.vol_shape), _stream(stream)),
+           "tnlm_energy_grad_bf16")
     return E.value, grad
 
 

@@ -760,31 +760,72 @@ tnlm_status tnlm_cgls(tnlm_geometry *geo, const float *y, float *x, int n_iter, 
     return TNLM_OK;
 }
 
-tnlm_status tnlm_energy_grad(tnlm_geometry *geo, const float *y, const float *f, const float *a,
-                             const tnlm_params *p, double *energy, float *grad, void *stream)
+}  // extern "C"
+
+// TNLM part of the energy for each storage type (BF16: box-sum (d, M) only)
+static tnlm_status energy_tnlm_t(const KGeom &kg, const float *a, const float *f, const tnlm_params *p, float *lam,
+                                 float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st)
+{
+    return launch_energy_tnlm(kg.nx, kg.ny, kg.nz, kg.np, a, f, p->d, p->M, p->h, lam, t1, grad, jpart, nblk, st);
+}
+
+static tnlm_status energy_tnlm_t(const KGeom &kg, const uint16_t *a, const uint16_t *f, const tnlm_params *p,
+                                 float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st)
+{
+    cudaError_t err = cudaSuccess;
+    if (!launch_energy_box_bf16(p->d, p->M, kg.nx, kg.ny, kg.nz, kg.np, a, f, p->h, lam, t1, grad, jpart, nblk, st,
+                                &err)) {
+        set_error("BF16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", p->d, p->M);
+        return TNLM_ERR_NOT_IMPLEMENTED;
+    }
+    TNLM_TRY_CUDA(err);
+    return TNLM_OK;
+}
+
+template <class T>
+static tnlm_status energy_grad_t(tnlm_geometry *geo, const T *y, const T *f, const T *a, const tnlm_params *p,
+                                 double *energy, float *grad, void *stream)
 {
     if (!geo || !y || !f || !a || !p || !energy || !grad)
         return arg_error("geometry, y, f, a, params, energy and grad must not be NULL");
     const KGeom &kg = geo->kg;
     TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
-    if (grad == f || grad == a) return arg_error("grad must not alias f or a");
+    if ((const void *)grad == (const void *)f || (const void *)grad == (const void *)a)
+        return arg_error("grad must not alias f or a");
     TNLM_TRY(ensure_workspace(geo, true, 4));
-    const long long nblk = energy_blocks(kg.nx, kg.ny, kg.nz, kg.np);
-    if (!geo->d_epart) TNLM_TRY(dev_alloc(&geo->d_epart, (size_t)nblk));
+    if (!geo->d_epart) {
+        const long long n1 = energy_blocks(kg.nx, kg.ny, kg.nz, kg.np), n2 = energy_box_blocks(kg.nx, kg.ny, kg.nz, kg.np);
+        TNLM_TRY(dev_alloc(&geo->d_epart, (size_t)(n1 > n2 ? n1 : n2)));
+    }
     cudaStream_t st = as_stream(stream);
     // fidelity: r|D| and ||P f - y||^2; grad = mu P^T (P f - y)
     TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, f, y, geo->d_r, geo->d_part, 1, st));
     TNLM_TRY(launch_sum_partials(geo->d_part, forward_blocks(kg, geo->n_views_total), geo->d_scalars, st));
     TNLM_TRY(launch_backproject(kg, geo->d_views, geo->d_view_off, geo->d_r, grad, grad, p->mu, 0.0f, true,
                                 prefix_workspace(geo), geo->n_views_total, st));
-    // TNLM part with frozen weights from a
-    TNLM_TRY(launch_energy_tnlm(kg.nx, kg.ny, kg.nz, kg.np, a, f, p->d, p->M, p->h, geo->d_tmp, grad, geo->d_epart, st));
+    // TNLM part with frozen weights from a (normalisers in d_tmp, the weighted means T1 in d_g)
+    long long nblk = 0;
+    TNLM_TRY(energy_tnlm_t(kg, a, f, p, geo->d_tmp, geo->d_g, grad, geo->d_epart, &nblk, st));
     TNLM_TRY(launch_sum_partials(geo->d_epart, nblk, geo->d_scalars + 1, st));
     double sc[2];
     TNLM_TRY_CUDA(cudaMemcpyAsync(sc, geo->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost, st));
     TNLM_TRY_CUDA(cudaStreamSynchronize(st));
     *energy = 0.5 * (double)p->mu * sc[0] + 0.5 * sc[1];
     return TNLM_OK;
+}
+
+extern "C" {
+
+tnlm_status tnlm_energy_grad(tnlm_geometry *geo, const float *y, const float *f, const float *a,
+                             const tnlm_params *p, double *energy, float *grad, void *stream)
+{
+    return energy_grad_t<float>(geo, y, f, a, p, energy, grad, stream);
+}
+
+tnlm_status tnlm_energy_grad_bf16(tnlm_geometry *geo, const uint16_t *y, const uint16_t *f, const uint16_t *a,
+                                  const tnlm_params *p, double *energy, float *grad, void *stream)
+{
+    return energy_grad_t<uint16_t>(geo, y, f, a, p, energy, grad, stream);
 }
 
 tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,

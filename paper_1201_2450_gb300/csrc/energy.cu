@@ -372,8 +372,14 @@ long long energy_blocks(int nx, int ny, int nz, int np)
 }
 
 tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, const float *f, int d, int M, float h,
-                               float *lam, float *grad, double *jpart, cudaStream_t st)
+                               float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st)
 {
+    // the box-sum form for the (d, M) it is compiled for, the direct tiled form otherwise
+    cudaError_t err = cudaSuccess;
+    if (launch_energy_box(d, M, nx, ny, nz, np, a, f, h, lam, t1, grad, jpart, nblk, st, &err)) {
+        TNLM_TRY_CUDA(err);
+        return TNLM_OK;
+    }
     const int ntz = (nz + kTZ - 1) / kTZ;
     dim3 block(kTX, kTY, kTZ), grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, np * ntz);
     const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
@@ -388,6 +394,7 @@ tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, c
     TNLM_TRY_CUDA(cudaGetLastError());
     k_energy_grad<<<grid, block, s2, st>>>(nx, ny, nz, np, ntz, a, f, lam, d, M, c2, grad, jpart);
     TNLM_TRY_CUDA(cudaGetLastError());
+    *nblk = energy_blocks(nx, ny, nz, np);
     return TNLM_OK;
 }
 

@@ -1,0 +1,319 @@
+// The TNLM half of the total energy and its gradient with frozen weights
+// (see energy.cu for the formulas) on the box-sum machinery of the sweep:
+// the same thread layout, the same separable patch sums and therefore the
+// same patch distance for a pair whichever of its two voxels is the output.
+//   pass 0, output x in phase i, candidates in phase i+1, x's own normaliser:
+//     Lambda_i(x) = log2 Z_i(x), T1_i(x) = sum_delta w f_{i+1}(x+delta),
+//     J_x = sum_delta w (f_i(x) - f_{i+1}(x+delta))^2 (FP64 block partials);
+//   pass 1, output x in phase i, candidates y = x+delta in phase i-1, each
+//     weighted by its own normaliser: w = 2^(-t - Lambda_{i-1}(y)) <= 1,
+//     grad_i(x) += f_i(x) (1 + sum w) - T1_i(x) - sum w f_{i-1}(y).
+#include "sweep_box.cuh"
+
+namespace tnlm {
+namespace box {
+
+template <int D_, int M_, int BZ, int WY_, int WZ_, bool INTERIOR, int PASS>
+__device__ __forceinline__ void box_energy(const float2 (&ai)[BZ + 2 * D_][(2 + 2 * D_) / 2], const float *s_aj,
+                                           const float *s_vj, const float *s_nl, const float2 (&fi)[BZ], int lane,
+                                           int wy, int wz, int x, int yb, int zb, int nx, int ny, int nz, float c2,
+                                           float2 (&o1)[BZ], float2 (&o2)[BZ], float2 (&o3)[BZ])
+{
+    constexpr int BY = 2;
+    using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
+    constexpr int SP = C::SY / 2;
+    float2 mref[BZ], N[BZ], Z[BZ], Q[BZ];
+#pragma unroll
+    for (int k = 0; k < BZ; ++k) {
+        mref[k] = make_float2(FLT_MAX, FLT_MAX);
+        N[k] = Z[k] = Q[k] = make_float2(0.f, 0.f);
+    }
+    const float2 nc2 = make_float2(-c2, -c2);
+    for (int dy = -M_; dy <= M_; ++dy) {
+        const bool vy0 = INTERIOR || (unsigned)(yb + dy) < (unsigned)ny;
+        const bool vy1 = INTERIOR || (unsigned)(yb + 1 + dy) < (unsigned)ny;
+        for (int dx = -M_; dx <= M_; ++dx) {
+            const bool vx = INTERIOR || (unsigned)(x + dx) < (unsigned)nx;
+            const bool vxy0 = vx && vy0, vxy1 = vx && vy1;
+            const float *paj = s_aj + (wy * BY + dy + M_) * C::AJX + lane + dx + M_;
+            const int vo = (wy * BY + dy + M_) * C::VJX + lane + dx + M_;
+            float2 aw[2 * M_ + C::SZ][SP];
+            float2 vw[2 * M_ + BZ], lw[2 * M_ + BZ];
+#pragma unroll
+            for (int r = 0; r < C::SZ - 1; ++r)
+#pragma unroll
+                for (int p = 0; p < SP; ++p) {
+                    const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
+                    aw[r][p] = make_float2(q0[0], q0[C::AJX]);
+                }
+#pragma unroll
+            for (int r = 0; r < BZ - 1; ++r) {
+                const int o = vo + (wz * BZ + r) * C::VJY * C::VJX;
+                vw[r] = make_float2(s_vj[o], s_vj[o + C::VJX]);
+                if (PASS == 1) lw[r] = make_float2(s_nl[o], s_nl[o + C::VJX]);
+            }
+#pragma unroll
+            for (int q = 0; q <= 2 * M_; ++q) {  // q = dz + M
+                {
+                    const int r = q + C::SZ - 1;
+#pragma unroll
+                    for (int p = 0; p < SP; ++p) {
+                        const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
+                        aw[r][p] = make_float2(q0[0], q0[C::AJX]);
+                    }
+                    const int rv = q + BZ - 1;
+                    const int o = vo + (wz * BZ + rv) * C::VJY * C::VJX;
+                    vw[rv] = make_float2(s_vj[o], s_vj[o + C::VJX]);
+                    if (PASS == 1) lw[rv] = make_float2(s_nl[o], s_nl[o + C::VJX]);
+                }
+                float2 bz[BZ][SP];
+#pragma unroll
+                for (int p = 0; p < SP; ++p) {
+                    float2 sq[C::SZ];
+#pragma unroll
+                    for (int zz = 0; zz < C::SZ; ++zz) {
+                        const float2 t = __fadd2_rn(ai[zz][p], make_float2(-aw[q + zz][p].x, -aw[q + zz][p].y));
+                        sq[zz] = __fmul2_rn(t, t);
+                    }
+#pragma unroll
+                    for (int k = 0; k < BZ; ++k) {
+                        float2 acc = sq[k];
+#pragma unroll
+                        for (int t = 1; t <= 2 * D_; ++t) acc = __fadd2_rn(acc, sq[k + t]);
+                        bz[k][p] = acc;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < BZ; ++k) {
+                    float m = bz[k][0].y;
+#pragma unroll
+                    for (int yy = 2; yy <= 2 * D_; ++yy) m += (yy & 1) ? bz[k][yy / 2].y : bz[k][yy / 2].x;
+                    const float2 yb2 = make_float2(bz[k][0].x + m, m + bz[k][SP - 1].y);
+                    const float2 Dv = xbox2<D_>(yb2);
+                    const bool vz = INTERIOR || (unsigned)(zb + k + q - M_) < (unsigned)nz;
+                    if (PASS == 0) {
+                        float2 a = __ffma2_rn(Dv, nc2, mref[k]);
+                        if (!INTERIOR) {
+                            if (!(vxy0 && vz)) a.x = -FLT_MAX;
+                            if (!(vxy1 && vz)) a.y = -FLT_MAX;
+                        }
+                        if (fmaxf(a.x, a.y) > kRescale) {
+                            if (a.x > kRescale) {
+                                const float sc = ex2(-a.x);
+                                N[k].x *= sc;
+                                Z[k].x *= sc;
+                                Q[k].x *= sc;
+                                mref[k].x = Dv.x * c2;
+                                a.x = 0.f;
+                            }
+                            if (a.y > kRescale) {
+                                const float sc = ex2(-a.y);
+                                N[k].y *= sc;
+                                Z[k].y *= sc;
+                                Q[k].y *= sc;
+                                mref[k].y = Dv.y * c2;
+                                a.y = 0.f;
+                            }
+                        }
+                        const float2 e = make_float2(ex2(a.x), ex2(a.y));
+                        const float2 v = vw[q + k];
+                        const float2 df = __fadd2_rn(fi[k], make_float2(-v.x, -v.y));
+                        N[k] = __ffma2_rn(e, v, N[k]);
+                        Z[k] = __fadd2_rn(Z[k], e);
+                        Q[k] = __ffma2_rn(e, __fmul2_rn(df, df), Q[k]);
+                    } else {
+                        // weight of the candidate's own normalisation: 2^(-t - Lambda(y)) <= 1
+                        float2 a = __ffma2_rn(Dv, nc2, lw[q + k]);
+                        if (!INTERIOR) {
+                            if (!(vxy0 && vz)) a.x = -FLT_MAX;
+                            if (!(vxy1 && vz)) a.y = -FLT_MAX;
+                        }
+                        const float2 e = make_float2(ex2(a.x), ex2(a.y));
+                        N[k] = __ffma2_rn(e, vw[q + k], N[k]);
+                        Z[k] = __fadd2_rn(Z[k], e);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < BZ; ++k) {
+        if (PASS == 0) {
+            o1[k] = make_float2(N[k].x / Z[k].x, N[k].y / Z[k].y);
+            o2[k] = make_float2(log2f(Z[k].x) - mref[k].x, log2f(Z[k].y) - mref[k].y);
+            o3[k] = make_float2(Q[k].x / Z[k].x, Q[k].y / Z[k].y);
+        } else {
+            o1[k] = N[k];
+            o2[k] = Z[k];
+        }
+    }
+}
+
+template <int D_, int M_, int BZ, int WY_, int WZ_, class T, int PASS>
+__global__ void __launch_bounds__(BoxCfg<D_, M_, 2, BZ, WY_, WZ_>::NT)
+    k_energy_box(int nx, int ny, int nz, int np, int ntx, int nty, int ntz, const T *__restrict__ a,
+                 const T *__restrict__ f, float *__restrict__ lam, float *__restrict__ t1, float *__restrict__ grad,
+                 double *__restrict__ jpart, float c2)
+{
+    constexpr int BY = 2;
+    using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
+    extern __shared__ float sm[];
+    float *s_aj = sm;
+    float *s_vj = s_aj + C::AJX * C::AJY * C::AJZ;
+    float *s_nl = s_vj + C::VJX * C::VJY * C::VJZ;  // pass 1: -Lambda of the neighbour phase
+    __shared__ double ws[C::NT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wy = warp % C::WY, wz = warp / C::WY;
+    int b = blockIdx.x;
+    const int tx_i = b % ntx;
+    b /= ntx;
+    const int ty_i = b % nty;
+    b /= nty;
+    const int tz_i = b % ntz;
+    const int i = b / ntz;
+    const int X0 = tx_i * C::TXO, Y0 = ty_i * C::TY, Z0 = tz_i * C::TZ;
+    const int x = X0 - D_ + lane;
+    const int yb = Y0 + wy * BY, zb = Z0 + wz * BZ;
+    const long long nvox = (long long)nx * ny * nz;
+    const bool interior = X0 - M_ >= 0 && X0 + C::TXO - 1 + M_ < nx && Y0 - M_ >= 0 && Y0 + C::TY - 1 + M_ < ny &&
+                          Z0 - M_ >= 0 && Z0 + C::TZ - 1 + M_ < nz;
+    const int jp = PASS == 0 ? (i + 1) % np : (i - 1 + np) % np;
+
+    float2 ai[C::SZ][C::SY / 2];
+    float2 fi[BZ];
+    {
+        const T *src = a + i * nvox, *fs = f + i * nvox;
+        const int cx = clampi(x, nx);
+#pragma unroll
+        for (int zz = 0; zz < C::SZ; ++zz)
+#pragma unroll
+            for (int p = 0; p < C::SY / 2; ++p) {
+                const long long zo = (long long)clampi(zb - D_ + zz, nz) * ny;
+                ai[zz][p] = make_float2(ld(src + (zo + clampi(yb - D_ + 2 * p, ny)) * nx + cx),
+                                        ld(src + (zo + clampi(yb - D_ + 2 * p + 1, ny)) * nx + cx));
+            }
+#pragma unroll
+        for (int k = 0; k < BZ; ++k) {
+            const long long zo = (long long)clampi(zb + k, nz) * ny;
+            fi[k] = make_float2(ld(fs + (zo + clampi(yb, ny)) * nx + cx), ld(fs + (zo + clampi(yb + 1, ny)) * nx + cx));
+        }
+    }
+    stage_clamped(s_aj, a + jp * nvox, X0 - D_ - M_, Y0 - D_ - M_, Z0 - D_ - M_, C::AJX, C::AJY, C::AJZ, nx, ny, nz,
+                  tid, C::NT);
+    stage_clamped(s_vj, f + jp * nvox, X0 - D_ - M_, Y0 - M_, Z0 - M_, C::VJX, C::VJY, C::VJZ, nx, ny, nz, tid, C::NT);
+    if (PASS == 1) {
+        const float *lj = lam + jp * nvox;
+        const int ox = X0 - D_ - M_, oy = Y0 - M_, oz = Z0 - M_;
+        for (int t = tid; t < C::VJX * C::VJY * C::VJZ; t += C::NT) {
+            const int lx = t % C::VJX, ly = (t / C::VJX) % C::VJY, lz = t / (C::VJX * C::VJY);
+            s_nl[t] = -__ldg(lj + ((long long)clampi(oz + lz, nz) * ny + clampi(oy + ly, ny)) * nx + clampi(ox + lx, nx));
+        }
+    }
+    __syncthreads();
+    float2 o1[BZ], o2[BZ], o3[BZ];
+    if (interior)
+        box_energy<D_, M_, BZ, WY_, WZ_, true, PASS>(ai, s_aj, s_vj, s_nl, fi, lane, wy, wz, x, yb, zb, nx, ny, nz, c2,
+                                                     o1, o2, o3);
+    else
+        box_energy<D_, M_, BZ, WY_, WZ_, false, PASS>(ai, s_aj, s_vj, s_nl, fi, lane, wy, wz, x, yb, zb, nx, ny, nz, c2,
+                                                      o1, o2, o3);
+    double jsum = 0.0;
+    if (lane >= D_ && lane < 32 - D_ && x < nx) {
+#pragma unroll
+        for (int j = 0; j < BY; ++j)
+#pragma unroll
+            for (int k = 0; k < BZ; ++k) {
+                const int y = yb + j, z = zb + k;
+                if (y < ny && z < nz) {
+                    const long long o = i * nvox + ((long long)z * ny + y) * nx + x;
+                    const float v1 = j == 0 ? o1[k].x : o1[k].y, v2 = j == 0 ? o2[k].x : o2[k].y;
+                    if (PASS == 0) {
+                        t1[o] = v1;
+                        lam[o] = v2;
+                        jsum += (double)(j == 0 ? o3[k].x : o3[k].y);
+                    } else {
+                        const float fo = j == 0 ? fi[k].x : fi[k].y;
+                        grad[o] += fo * (1.f + v2) - t1[o] - v1;
+                    }
+                }
+            }
+    }
+    if (PASS == 0) {
+        for (int off = 16; off > 0; off >>= 1) jsum += __shfl_down_sync(0xffffffffu, jsum, off);
+        if (lane == 0) ws[warp] = jsum;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < C::NT / 32; ++w) s += ws[w];
+            jpart[blockIdx.x] = s;
+        }
+    }
+}
+
+template <int D_, int M_, class T>
+bool launch_energy_dm(int nx, int ny, int nz, int np, const T *a, const T *f, float c2, float *lam, float *t1,
+                      float *grad, double *jpart, long long *nblk, cudaStream_t st, cudaError_t *err)
+{
+    using S = BoxShape<0>;
+    using C = BoxCfg<D_, M_, 2, S::BZ, S::WY, S::WZ>;
+    const int ntx = (nx + C::TXO - 1) / C::TXO, nty = (ny + C::TY - 1) / C::TY, ntz = (nz + C::TZ - 1) / C::TZ;
+    const long long blocks = (long long)ntx * nty * ntz * np;
+    if (blocks > 0x7fffffffLL) return false;
+    *nblk = blocks;
+    const size_t smem = C::SMEM + sizeof(float) * (size_t)C::VJX * C::VJY * C::VJZ;
+    auto k0 = k_energy_box<D_, M_, S::BZ, S::WY, S::WZ, T, 0>;
+    auto k1 = k_energy_box<D_, M_, S::BZ, S::WY, S::WZ, T, 1>;
+    if ((*err = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return true;
+    if ((*err = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return true;
+    k0<<<(unsigned)blocks, C::NT, smem, st>>>(nx, ny, nz, np, ntx, nty, ntz, a, f, lam, t1, grad, jpart, c2);
+    if ((*err = cudaGetLastError()) != cudaSuccess) return true;
+    k1<<<(unsigned)blocks, C::NT, smem, st>>>(nx, ny, nz, np, ntx, nty, ntz, a, f, lam, t1, grad, jpart, c2);
+    *err = cudaGetLastError();
+    return true;
+}
+
+template <class T>
+bool launch_energy(int d, int M, int nx, int ny, int nz, int np, const T *a, const T *f, float c2, float *lam,
+                   float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st, cudaError_t *err)
+{
+#define TNLM_EBOX_CASE(DD, MM)                                                                                      \
+    if (d == DD && M == MM) return launch_energy_dm<DD, MM, T>(nx, ny, nz, np, a, f, c2, lam, t1, grad, jpart, nblk, \
+                                                                 st, err);
+    TNLM_EBOX_CASE(1, 1)
+    TNLM_EBOX_CASE(1, 2)
+    TNLM_EBOX_CASE(1, 3)
+    TNLM_EBOX_CASE(2, 1)
+    TNLM_EBOX_CASE(2, 2)
+    TNLM_EBOX_CASE(2, 3)
+#undef TNLM_EBOX_CASE
+    return false;
+}
+
+}  // namespace box
+
+long long energy_box_blocks(int nx, int ny, int nz, int np)
+{
+    // the smallest tile of the box layout (d = 2) gives the largest count
+    using C = box::BoxCfg<2, 1, 2, box::BoxShape<0>::BZ, box::BoxShape<0>::WY, box::BoxShape<0>::WZ>;
+    return (long long)((nx + C::TXO - 1) / C::TXO) * ((ny + C::TY - 1) / C::TY) * ((nz + C::TZ - 1) / C::TZ) * np;
+}
+
+bool launch_energy_box(int d, int M, int nx, int ny, int nz, int np, const float *a, const float *f, float h,
+                       float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st,
+                       cudaError_t *err)
+{
+    const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    return box::launch_energy<float>(d, M, nx, ny, nz, np, a, f, c2, lam, t1, grad, jpart, nblk, st, err);
+}
+
+bool launch_energy_box_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *a, const uint16_t *f,
+                            float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
+                            cudaStream_t st, cudaError_t *err)
+{
+    using B = __nv_bfloat16;
+    const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    return box::launch_energy<B>(d, M, nx, ny, nz, np, reinterpret_cast<const B *>(a), reinterpret_cast<const B *>(f),
+                                 c2, lam, t1, grad, jpart, nblk, st, err);
+}
+
+}  // namespace tnlm

@@ -125,7 +125,16 @@ size_t energy_weights_grad_floats(int nx, int ny, int nz, int d, int M);
 tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
                                        float h, float *grad_a, float *ws, cudaStream_t st);
 tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, const float *f, int d, int M, float h,
-                               float *lam, float *grad, double *jpart, cudaStream_t st);
+                               float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st);
+// Box-sum form of the energy's TNLM part (energy_box.cu); false when (d, M) has no box kernel.  lam, t1:
+// np * nvox floats of scratch; grad accumulates; jpart receives *nblk FP64 partial sums of J.
+long long energy_box_blocks(int nx, int ny, int nz, int np);
+bool launch_energy_box(int d, int M, int nx, int ny, int nz, int np, const float *a, const float *f, float h,
+                       float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st,
+                       cudaError_t *err);
+bool launch_energy_box_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *a, const uint16_t *f,
+                            float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
+                            cudaStream_t st, cudaError_t *err);
 long long energy_blocks(int nx, int ny, int nz, int np);
 
 // FDK of every phase from its own views (fdk.cu); filt: projection-sized scratch.

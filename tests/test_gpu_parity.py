@@ -555,6 +555,23 @@ def test_energy_grad_two_phases(ora):
     assert rel_l2(g.cpu().numpy(), g_ref) <= RTOL
 
 
+@pytest.mark.parametrize("d, M", [(1, 2), (2, 1), (1, 3)])
+def test_energy_grad_bf16_equals_fp32_on_widened_inputs(d, M):
+    """BF16 storage of y, f and a: every value is widened before use and the
+    gradient is FP32, so the call equals the FP32 call on the widened inputs
+    bit for bit (energy and gradient)."""
+    geom = GEOMS["ragged_uneven"]
+    G = tnlm.Geometry(geom)
+    a, f, y = _energy_inputs(G.vol_shape, G.proj_shape, 240)
+    a16, f16, y16 = cuda(a).bfloat16(), cuda(f).bfloat16(), cuda(y).bfloat16()
+    p = tnlm.Params(d=d, M=M, h=0.03, mu=0.7)
+    E16, g16 = tnlm.tnlm_energy_grad_bf16(G, y16, f16, a16, p)
+    E32, g32 = tnlm.tnlm_energy_grad(G, y16.float(), f16.float(), a16.float(), p)
+    torch.cuda.synchronize()
+    assert E16 == E32
+    assert torch.equal(g16, g32)
+
+
 def test_energy_autograd_and_directional_derivatives(ora):
     """TNLMEnergy in autograd: f.grad is the kernels' gradient, and along 64
     random directions it matches FP64 central differences of the oracle's
