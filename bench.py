@@ -48,10 +48,10 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
     # the transpose stage is the column scan plus the band kernel
-    "k_forward": {"bytes_per_launch": int((273.490432e6 + 147.899392e6) * 10 / 6), "source_sha": "c76a4c3629b9ff59"},
-    "k_backproject": {"bytes_per_launch": int((169.964544e6 + 285.275136e6 + 557.31456e6 + 93.097984e6) * 10 / 6),
+    "k_forward": {"bytes_per_launch": int((273.283328e6 + 147.624448e6) * 10 / 6), "source_sha": "c76a4c3629b9ff59"},
+    "k_backproject": {"bytes_per_launch": int((169.898496e6 + 284.921856e6 + 556.747264e6 + 92.790784e6) * 10 / 6),
                       "source_sha": "c76a4c3629b9ff59"},
-    "k_sweep": {"bytes_per_launch": int((162.90304e6 + 84.224256e6) * 10 / 6), "source_sha": "4e8b41aeca19e017"},
+    "k_sweep": {"bytes_per_launch": int((159.0528e6 + 83.814912e6) * 10 / 6), "source_sha": "19521b83f7940da1"},
 }
 
 
@@ -413,6 +413,8 @@ def measure_variants(tnlm, synth, geom, y, stream, params) -> dict:
     g, _ = synth.enhance_input(c3, device="cuda")
     f = torch.empty_like(g)
     p = tnlm.Params(d=c3.d, M=c3.M, h=c3.h, mu=c3.mu, n_outer=1, clip_nonneg=0)
+    out["tnlm_e_sweep_shape"] = tnlm.tnlm_autotune_sweep(tuple(g.shape), c3.d, c3.M, c3.h)
+    out["tnlm_e_bf16_sweep_shape"] = tnlm.tnlm_autotune_sweep(tuple(g.shape), c3.d, c3.M, c3.h, bf16=True)
     sweep_ms = _time_ms(lambda: tnlm.tnlm_enhance(g, p, out=f), stream, reps=2)
     nvox = c3.n_phases * c3.vol[0] * c3.vol[1] * c3.vol[2]
     out["tnlm_e_workload"] = "TNLM-E FP32 10 x 512x512x128, patch 5^3, window 7^3, h 0.04, mu 1"
