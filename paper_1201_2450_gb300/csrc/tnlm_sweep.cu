@@ -1,6 +1,9 @@
 // TNLM step of the method: the patch-similarity weights of Eq. 9 fused into
-// one Gauss-Jacobi sweep of Eq. 8 (k_sweep), and an explicit export of the
-// normalised weights (k_weights).
+// one Gauss-Jacobi sweep of Eq. 8.  The box-sum kernels (sweep_box.cuh, one
+// translation unit per launch shape) cover d in {1,2}, M in {1,2,3}; this
+// file holds the direct tiled form for the other (d, M) (k_sweep), the
+// explicit export of the normalised weights (k_weights), the launch-shape
+// table and the sweep launchers.
 //
 // Readings of the paper used here: weights are normalised over the search
 // window separately for each voxel and each direction (i+1, i-1); patch reads
@@ -11,8 +14,6 @@
 // 2^(m - t) / sum 2^(m - t) for any reference m, and the reference only moves
 // (rescaling the running sums) when a candidate beats it by more than
 // kRescale, so no weight overflows and the largest weight is >= 1.
-#include <cuda_bf16.h>
-
 #include <cfloat>
 #include <cmath>
 
@@ -33,24 +34,16 @@ __device__ __forceinline__ float ex2(float x)
 
 __device__ __forceinline__ int clampi(int a, int n) { return a < 0 ? 0 : (a >= n ? n - 1 : a); }
 
-// Storage types of the images: FP32, or BF16 (widened to FP32 on load; every
-// sum, weight and normaliser stays FP32; the output is rounded to BF16).
-__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-__device__ __forceinline__ void st(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-
 // Stage the box [o0, o0 + ext) of one phase image into shared memory with
 // coordinates clamped to the volume.
-template <class T>
-__device__ __forceinline__ void stage_clamped(float *dst, const T *__restrict__ src, int ox, int oy, int oz,
+__device__ __forceinline__ void stage_clamped(float *dst, const float *__restrict__ src, int ox, int oy, int oz,
                                               int ex, int ey, int ez, int nx, int ny, int nz, int tid, int nthr)
 {
     const int n = ex * ey * ez;
     for (int t = tid; t < n; t += nthr) {
         const int lx = t % ex, ly = (t / ex) % ey, lz = t / (ex * ey);
         const int gx = clampi(ox + lx, nx), gy = clampi(oy + ly, ny), gz = clampi(oz + lz, nz);
-        dst[t] = ld(src + ((long long)gz * ny + gy) * nx + gx);
+        dst[t] = __ldg(src + ((long long)gz * ny + gy) * nx + gx);
     }
 }
 
