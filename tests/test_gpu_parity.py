@@ -209,6 +209,21 @@ def test_enhance_matches_oracle(ora):
     assert rel_l2(tnlm.tnlm_enhance(cuda(g), p2).cpu().numpy(), ora.enhance(g, 1, 2, 0.04, 1.0, 2)) <= RTOL
 
 
+C3_TINY = synth.EnhanceConfig("TNLM-E reduced 10x20x20x8", 10, (20, 20, 8), 9.6, 0.002, 0.003, 36, 2, 3, 0.04, 1.0, 30,
+                              1003)
+
+
+def test_enhance_c3_structure_full_length(ora):
+    """C3's structure (10 phases, patch 5^3, window 7^3, h = 0.04) for its full 30 sweeps on a reduced grid."""
+    cfg = C3_TINY
+    g, _ = synth.enhance_input(cfg)
+    g = g.numpy()
+    p = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, n_outer=cfg.n_sweeps, clip_nonneg=0)
+    f = tnlm.tnlm_enhance(cuda(g), p).cpu().numpy()
+    ref = ora.enhance(g, cfg.d, cfg.M, cfg.h, cfg.mu, cfg.n_sweeps)
+    assert rel_l2(f, ref) <= RTOL
+
+
 def _recon_case(ora, cfg, n_outer, seed=7):
     pb = synth.recon_problem(cfg)
     OG = ora.Geometry(pb.geom)
