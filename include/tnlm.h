@@ -274,7 +274,7 @@ tnlm_status tnlm_energy_grad_bf16(tnlm_geometry *geom, const uint16_t *y, const 
  * a = f gives the gradient of the energy whose weights are computed from f
  * itself.  f, a, grad_a: [N_p][nz][ny][nx] FP32 device arrays; grad_a is
  * overwritten and must not alias f or a.  Allocates
- * (2M+1)^3 (nx ny nz + (nx+2d)(ny+2d)(nz+2d)) floats stream-ordered
+ * (2M+1)^3 (nx ny nz + (nx+2d)(ny+2d)(nz+2d)) + 2 N_p nx ny nz floats stream-ordered
  * (cudaMallocAsync) per call and processes the phase pairs (i, i+1) in
  * order on `stream`.  The paper minimises Eq. 1 but never differentiates its
  * weights; this serves gradient-based use of the energy. */

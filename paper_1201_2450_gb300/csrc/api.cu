@@ -835,7 +835,7 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int np, const float
     if (!f || !a || !grad_a) return arg_error("f, a and grad_a must not be NULL");
     if (grad_a == f || grad_a == a) return arg_error("grad_a must not alias f or a");
     cudaStream_t st = as_stream(stream);
-    const size_t n = energy_weights_grad_floats(nx, ny, nz, d, M);
+    const size_t n = energy_weights_grad_floats(nx, ny, nz, np, d, M);
     float *ws = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), sizeof(float) * n, st) != cudaSuccess) {
         cudaGetLastError();

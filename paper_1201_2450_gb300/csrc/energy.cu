@@ -328,10 +328,28 @@ __global__ void __launch_bounds__(256) k_wa_gather(int nx, int ny, int nz, int d
 
 }  // namespace
 
-size_t energy_weights_grad_floats(int nx, int ny, int nz, int d, int M)
+size_t energy_weights_grad_floats(int nx, int ny, int nz, int np, int d, int M)
 {
     const size_t W = (size_t)(2 * M + 1) * (2 * M + 1) * (2 * M + 1);
-    return W * ((size_t)nx * ny * nz + (size_t)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d));
+    const size_t nvox = (size_t)nx * ny * nz;
+    // G and its box sum B, then the box path's normalisers and weighted means of q (all phases)
+    return W * (nvox + (size_t)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d)) + 2 * (size_t)np * nvox;
+}
+
+tnlm_status launch_wa_box_gather(int nx, int ny, int nz, int np, int i, int d, int M, const float *a, const float *G,
+                                 float *B, float *grad_a, cudaStream_t st)
+{
+    const long long nvox = (long long)nx * ny * nz;
+    const int S = 2 * M + 1, W = S * S * S;
+    const long long pn = (long long)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d);
+    const int j = (i + 1) % np;
+    const float *ai = a + (long long)i * nvox, *aj = a + (long long)j * nvox;
+    k_wa_B<<<(unsigned)((pn + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, W, G, B);
+    TNLM_TRY_CUDA(cudaGetLastError());
+    k_wa_gather<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, M, ai, aj, B, grad_a + (long long)i * nvox,
+                                                                grad_a + (long long)j * nvox);
+    TNLM_TRY_CUDA(cudaGetLastError());
+    return TNLM_OK;
 }
 
 tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
@@ -341,6 +359,11 @@ tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const flo
     const int S = 2 * M + 1, W = S * S * S, R = M + d;
     float *G = ws, *B = ws + (size_t)W * nvox;
     const long long pn = (long long)(nx + 2 * d) * (ny + 2 * d) * (nz + 2 * d);
+    // the box-sum form of the normalisers and of G where it is compiled, the direct tiled form otherwise
+    float *lam = B + (size_t)W * pn, *qbar = lam + (size_t)np * nvox;
+    tnlm_status status = TNLM_OK;
+    if (launch_energy_weights_grad_box(d, M, nx, ny, nz, np, f, a, h, grad_a, ws, lam, qbar, st, &status))
+        return status;
     const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
     const float cg = (float)(0.5 / (2.0 * (double)h * (double)h));
     const size_t smem = sizeof(float) * ((size_t)(kTX + 2 * d) * (kTY + 2 * d) * (kTZ + 2 * d) +
@@ -356,13 +379,9 @@ tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const flo
         k_wa_G<<<grid, block, smem, st>>>(nx, ny, nz, ntz, ai, aj, f + (long long)i * nvox, f + (long long)j * nvox, d, M,
                                           c2, cg, G);
         TNLM_TRY_CUDA(cudaGetLastError());
-        k_wa_B<<<(unsigned)((pn + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, W, G, B);
-        TNLM_TRY_CUDA(cudaGetLastError());
-        k_wa_gather<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(nx, ny, nz, d, M, ai, aj, B,
-                                                                    grad_a + (long long)i * nvox,
-                                                                    grad_a + (long long)j * nvox);
-        TNLM_TRY_CUDA(cudaGetLastError());
+        TNLM_TRY(launch_wa_box_gather(nx, ny, nz, np, i, d, M, a, G, B, grad_a, st));
     }
+    (void)pn;
     return TNLM_OK;
 }
 

@@ -121,7 +121,14 @@ tnlm_status run_cgls(const CglsArgs &a, cudaStream_t st);
 // grad += TNLM gradient, jpart[energy_blocks()] <- FP64 partials of J.
 // Gradient of 1/2 sum J through the weights w.r.t. their source images a
 // (f fixed); ws holds energy_weights_grad_floats() floats; grad_a overwritten.
-size_t energy_weights_grad_floats(int nx, int ny, int nz, int d, int M);
+size_t energy_weights_grad_floats(int nx, int ny, int nz, int np, int d, int M);
+// box sum of G over the patch offsets and the gather onto both phases of the pair (i, i+1)
+tnlm_status launch_wa_box_gather(int nx, int ny, int nz, int np, int i, int d, int M, const float *a, const float *G,
+                                 float *B, float *grad_a, cudaStream_t st);
+// box-sum form of the normalisers and G (energy_box.cu); false when (d, M) has no box kernel
+bool launch_energy_weights_grad_box(int d, int M, int nx, int ny, int nz, int np, const float *f, const float *a,
+                                    float h, float *grad_a, float *ws, float *lam, float *qbar, cudaStream_t st,
+                                    tnlm_status *status);
 tnlm_status launch_energy_weights_grad(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,
                                        float h, float *grad_a, float *ws, cudaStream_t st);
 tnlm_status launch_energy_tnlm(int nx, int ny, int nz, int np, const float *a, const float *f, int d, int M, float h,
