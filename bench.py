@@ -289,6 +289,7 @@ def run_ours(args, rank, world, local):
     e_steps = max(1, min(args.steps, 5))
     for _ in range(e_steps):
         h2d, d2h = tnlm.reconstruct_host(geom, y_host, f_host, params, y_dev, f_dev)
+        stream.synchronize()  # the host reads this step's result before the next step starts
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = e_steps * world / e2e_s
