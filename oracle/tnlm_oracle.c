@@ -22,7 +22,11 @@
  *   - Gauss-Jacobi sweep    : Eq. 8
  *   - positivity correction : TNLM-R step 4 (Sec. 2.3)
  *   - TNLM-R / TNLM-E loops : the two algorithm boxes of Sec. 2.3
- *   - energies              : Eq. 1, Eq. 2, Eq. 4
+ *   - energies              : Eq. 1, Eq. 2, Eq. 4, and the gradient of Eq. 1
+ *                             with the weights frozen and through the
+ *                             weights (every term differentiated, scatter form)
+ *   - CGLS for (P1)         : ref. 37 as named in Sec. 2.3, phase by phase
+ *   - FDK                   : ref. 16 (Sec. 2.2-2.3), full-scan, per phase
  *
  * Readings where the paper is silent (each is also listed in the design
  * notes):
@@ -39,7 +43,7 @@
  *   R6 TNLM-R: the Gauss-Jacobi iterate starts at f^(l=0) = g^(k) (or at
  *      f^(k-1) with gj_start = 1); weights come from g^(k).
  *   R7 (P1) is solved by n_inner gradient steps g <- g - tau P^T (P g - y)
- *      started from f^(k-1), instead of CGLS.
+ *      or by n_inner CGLS iterations (p1_cgls), both started from f^(k-1).
  *   R8 voxels are half-open cells [lo, hi); a ray lying exactly in a cell
  *      face plane belongs to the cell whose lower face it lies in.
  *
