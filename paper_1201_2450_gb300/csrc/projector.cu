@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(kBpBX *kBpBY)
 }
 
 // Exclusive prefix sums along each detector column (fixed view and iu) of the
-// ray-length-scaled projection, accumulated in FP64 and stored as an
-// (hi, lo) float pair: pref[vg][iv][iu] = sum_{t < iv} r(t) |D(t)|.  A sum over
+// ray-length-scaled projection, accumulated in double-float arithmetic and
+// stored as an (hi, lo) float pair: pref[vg][iv][iu] = sum_{t < iv} r(t) |D(t)|.  A sum over
 // a run of rows is then two loads and a difference, exact to FP32 rounding.
 // For an unscaled input the scaled values are also written to scaled_out.
 template <bool SCALED>
@@ -390,7 +390,10 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
     const float *__restrict__ pc = proj + (long long)vg * G.npix + iu;
     float *__restrict__ so = SCALED ? nullptr : scaled_out + (long long)vg * G.npix + iu;
     float2 *__restrict__ po = pref + (long long)vg * (G.nv + 1) * G.nu + iu;
-    double acc = 0.0;
+    // running sum as an unevaluated pair hi + lo: each addition is split into its
+    // rounded result and exact error (Knuth's two-sum), the errors gather in lo;
+    // FP64 adds would cost far more issue slots on this GPU
+    float hi = 0.f, lo = 0.f;
     po[0] = make_float2(0.f, 0.f);
     for (int iv = 0; iv < G.nv; ++iv) {
         float r = __ldg(pc + (long long)iv * G.nu);
@@ -399,9 +402,11 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
             r *= sqrtf(len_u2 + v * v);
             so[(long long)iv * G.nu] = r;
         }
-        acc += (double)r;
-        const float hi = (float)acc;
-        po[(long long)(iv + 1) * G.nu] = make_float2(hi, (float)(acc - (double)hi));
+        const float t = hi + r;
+        const float bv = t - hi;
+        lo += (hi - (t - bv)) + (r - bv);
+        hi = t;
+        po[(long long)(iv + 1) * G.nu] = make_float2(hi, lo);
     }
 }
 
