@@ -153,14 +153,17 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             int ia = clamp_floor(fmaf(blo, Ga, Ea), na);
             int ib = clamp_floor(fmaf(blo, Gb, Eb), nb);
             int ic = clamp_floor(fmaf(blo, Gc, Ec), nc);
-            // next plane crossing on each axis, in the same form as the entry/exit test above so
-            // that exit planes compare equal to bhi; the plane coordinates are kept as exact float
-            // shadows of the integer indices (small integers), so no conversion per step
+            // next plane crossing on each axis, one FMA per step: beta = f * iv - E * iv, with the
+            // plane coordinates f kept as exact float shadows of the integer indices (small
+            // integers), so no conversion and no drift per step.  An exit plane may then differ
+            // from bhi by an ulp: slabs are counted separately, and a crossing an ulp past the
+            // exit only steps to an index whose load is guarded.
             float fa = (float)(ia + pa), fb = (float)(ib + pb), fc = (float)(ic + pc);
             const float saf = (float)sa, sbf = (float)sb, scf = (float)sc;
-            float ba = (fa - Ea) * iva;
-            float bb = Gb != 0.f ? (fb - Eb) * ivb : FLT_MAX;
-            float bc = Gc != 0.f ? (fc - Ec) * ivc : FLT_MAX;
+            const float oa = -Ea * iva, ob = -Eb * ivb, oc = -Ec * ivc;
+            float ba = fmaf(fa, iva, oa);
+            float bb = Gb != 0.f ? fmaf(fb, ivb, ob) : FLT_MAX;
+            float bc = Gc != 0.f ? fmaf(fc, ivc, oc) : FLT_MAX;
             // a-slabs visited: from the entry cell to the cell holding the exit point (a slab of zero
             // length at either end is harmless; every index stays inside the volume)
             const int ia_last = clamp_floor(fmaf(bhi, Ga, Ea), na);
@@ -169,10 +172,10 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             int idx = ia * ta + ib * tb + ic * tc;
             float fcur = ldg_v(fp + idx);
             float bcur = blo;
-            for (int k = 0; k < n_slabs; ++k) {
+            // one a-slab: its c and b crossings; true when the ray left the volume through c
+            auto slab = [&]() -> bool {
                 const float bend = fminf(ba, bhi);  // end of this a-slab inside the volume
                 if (bc < bend) {                    // c crossings (coherent across the warp, rare)
-                    bool out = false;
                     for (int rc = 0; rc < 4 && bc < bend; ++rc) {
                         if (bb < bc) {
                             acc = fmaf(fcur, bb - bcur, acc);
@@ -181,21 +184,17 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                             idx += sb * tb;
                             fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
                             fb += sbf;
-                            bb = (fb - Eb) * ivb;
+                            bb = fmaf(fb, ivb, ob);
                         }
                         acc = fmaf(fcur, bc - bcur, acc);
                         bcur = bc;
                         ic += sc;
-                        if ((unsigned)ic >= (unsigned)nc || (unsigned)ib >= (unsigned)nb) {
-                            out = true;
-                            break;
-                        }
+                        if ((unsigned)ic >= (unsigned)nc || (unsigned)ib >= (unsigned)nb) return true;
                         idx += sc * tc;
                         fcur = ldg_v(fp + idx);
                         fc += scf;
-                        bc = (fc - Ec) * ivc;
+                        bc = fmaf(fc, ivc, oc);
                     }
-                    if (out) break;
                 }
                 // at most one b crossing in the rest of the slab
                 const bool hit = bb < bend;
@@ -206,18 +205,25 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                     idx += sb * tb;
                     fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
                     fb += sbf;
-                    bb = (fb - Eb) * ivb;
+                    bb = fmaf(fb, ivb, ob);
                 }
                 acc = fmaf(fcur, bend - e1, acc);
                 bcur = bend;
-                if (k + 1 < n_slabs) {
-                    ia += sa;
-                    idx += sa * ta;
-                    fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
-                    fa += saf;
-                    ba = (fa - Ea) * iva;
+                return false;
+            };
+            // every slab but the last ends on an a-plane: step into the next one unconditionally
+            bool left = false;
+            for (int k = 1; k < n_slabs; ++k) {
+                if (slab()) {
+                    left = true;
+                    break;
                 }
+                idx += sa * ta;
+                fcur = (unsigned)ib < (unsigned)nb ? ldg_v(fp + idx) : 0.f;
+                fa += saf;
+                ba = fmaf(fa, iva, oa);
             }
+            if (!left) slab();
             acc *= len;
         }
         const long long o = ((long long)vg * G.nv + iv) * G.nu + iu;
