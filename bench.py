@@ -48,10 +48,10 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
     # the transpose stage is the column scan plus the band kernel
-    "k_forward": {"bytes_per_launch": int((274.427392e6 + 147.934720e6) * 10 / 6), "source_sha": "0b8d2b144e7b74a7"},
+    "k_forward": {"bytes_per_launch": int((272.985856e6 + 147.891456e6) * 10 / 6), "source_sha": "b3bfed95f4be8ebc"},
     # (the scan and band kernels are unchanged since their capture; only k_forward changed in this file)
     "k_backproject": {"bytes_per_launch": int((169.895936e6 + 284.310784e6 + 554.819840e6 + 92.989184e6) * 10 / 6),
-                      "source_sha": "0b8d2b144e7b74a7"},
+                      "source_sha": "b3bfed95f4be8ebc"},
     "k_sweep": {"bytes_per_launch": int((159.0528e6 + 83.814912e6) * 10 / 6), "source_sha": "19521b83f7940da1"},
 }
 

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             };
             // every slab but the last ends on an a-plane: step into the next one unconditionally
             bool left = false;
+#pragma unroll 2
             for (int k = 1; k < n_slabs; ++k) {
                 if (slab()) {
                     left = true;
