@@ -148,9 +148,9 @@ def job_throughput(steps: int, world: int, ms_max: float) -> float:
     reconstruction; the job takes the slowest rank's time."""
     return steps * world / (ms_max / 1e3)
 
-# algorithmic work and bytes per launch: each kernel's unit count times its per-unit bytes or operations
+
 # ---------------------------------------------------------------------------
-# algorithmic work and bytes per launch (see DESIGN.md, "Roofline")
+# algorithmic work and bytes per launch: each kernel's unit count times its per-unit bytes or operations
 # ---------------------------------------------------------------------------
 
 def algorithmic_bytes(cfg, n_views_total):
