@@ -2,10 +2,13 @@
 // Eq. 9 weights frozen, computed from weight-source images a) and its
 // gradient, for differentiable use:
 //   E(f)   = mu/2 sum_i ||P_i f_i - y_i||^2 + 1/2 sum_i J[f_i, f_{i+1}],
-//   grad_i = mu P_i^T (P_i f_i - y_i)
-//            + f_i (1 + c_{i-1}) - W_i f_{i+1} - W_{i-1}^T f_{i-1},
-// with W_i the row-normalised weights of phase i toward i+1 and c_{i-1} the
-// column sums of W_{i-1}.  The transposed term needs, at voxel y of phase i,
+//   grad_i(x) = mu (P_i^T (P_i f_i - y_i))(x)
+//               + sum_delta w_i(x, delta) (f_i(x) - f_{i+1}(x + delta))
+//               + sum_{y = x + delta'} w_{i-1}(y, x - y) (f_i(x) - f_{i-1}(y)),
+// with w_i the row-normalised weights of phase i toward i+1 (the second line
+// is W_i applied to the differences, the third the transposed term of
+// W_{i-1}); each pair adds its own difference, so nothing of size f cancels
+// when f is close to its weighted means.  The transposed term needs, at voxel y of phase i,
 // the weight that the voxel x = y + delta' of phase i-1 gives to y; it uses
 // x's own normaliser, so a first pass stores Lambda(x) = log2 Z(x) - m(x)
 // per voxel (k_lognorm) and the gradient pass (k_energy_grad) gathers both
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kNT) k_energy_grad(int nx, int ny, int nz, int
     const long long o = i * nvox + ((long long)clampi(z, nz) * ny + clampi(y, ny)) * nx + clampi(x, nx);
     const float fi = __ldg(f + o), li = __ldg(lam + o);
     stage(s_ai, a + i * nvox, X0 - d, Y0 - d, Z0 - d, kTX + 2 * d, kTY + 2 * d, kTZ + 2 * d, nx, ny, nz, tid);
-    float term1 = 0.f, term2 = 0.f, csum = 0.f, jy = 0.f;
+    float term1 = 0.f, term2 = 0.f, jy = 0.f;
     for (int dir = 0; dir < 2; ++dir) {
         const int j = dir == 0 ? (i + 1) % np : (i - 1 + np) % np;
         __syncthreads();
@@ -139,21 +142,20 @@ __global__ void __launch_bounds__(kNT) k_energy_grad(int nx, int ny, int nz, int
                     const float t = patch_dist(s_ai, s_aj, tx, ty, tz, dx, dy, dz, d, R) * c2;
                     const int q = ((tz + M + dz) * vjy + (ty + M + dy)) * vjx + (tx + M + dx);
                     const float fj = s_fj[q];
+                    const float df = fi - fj;
                     if (dir == 0) {  // this voxel's own weights toward phase i+1
                         const float w = ex2(-t - li);
-                        term1 = fmaf(w, fj, term1);
-                        const float df = fi - fj;
+                        term1 = fmaf(w, df, term1);
                         jy = fmaf(w, df * df, jy);
                     } else {  // weights of the phase i-1 voxel y+delta toward this voxel
                         const float w = ex2(-t - s_lj[q]);
-                        term2 = fmaf(w, fj, term2);
-                        csum += w;
+                        term2 = fmaf(w, df, term2);
                     }
                 }
             }
         }
     }
-    if (inside) grad[o] += fi * (1.f + csum) - term1 - term2;
+    if (inside) grad[o] += term1 + term2;
     // block partial of J (FP64)
     double v = inside ? (double)jy : 0.0;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);

@@ -3,11 +3,17 @@
 // the same thread layout, the same separable patch sums and therefore the
 // same patch distance for a pair whichever of its two voxels is the output.
 //   pass 0, output x in phase i, candidates in phase i+1, x's own normaliser:
-//     Lambda_i(x) = log2 Z_i(x), T1_i(x) = sum_delta w f_{i+1}(x+delta),
+//     Lambda_i(x) = log2 Z_i(x),
+//     T1_i(x) = sum_delta w (f_i(x) - f_{i+1}(x+delta)),
 //     J_x = sum_delta w (f_i(x) - f_{i+1}(x+delta))^2 (FP64 block partials);
 //   pass 1, output x in phase i, candidates y = x+delta in phase i-1, each
 //     weighted by its own normaliser: w = 2^(-t - Lambda_{i-1}(y)) <= 1,
-//     grad_i(x) += f_i(x) (1 + sum w) - T1_i(x) - sum w f_{i-1}(y).
+//     grad_i(x) += T1_i(x) + sum w (f_i(x) - f_{i-1}(y)).
+// Every pair contributes its own difference f_i(x) - f_j(y), as in the scatter
+// form of the gradient, so no term of size f has to cancel against another:
+// near a fixed point of Eq. 8 (f close to its weighted means) the gradient is
+// small against f and a form such as f (1 + sum w) - sum w f_j would lose the
+// digits that matter.
 #include "sweep_box.cuh"
 
 namespace tnlm {
@@ -118,7 +124,7 @@ __device__ __forceinline__ void box_energy(const float2 (&ai)[BZ + 2 * D_][(2 + 
                         const float2 e = make_float2(ex2(a.x), ex2(a.y));
                         const float2 v = vw[q + k];
                         const float2 df = __fadd2_rn(fi[k], make_float2(-v.x, -v.y));
-                        N[k] = __ffma2_rn(e, v, N[k]);
+                        N[k] = __ffma2_rn(e, df, N[k]);
                         Z[k] = __fadd2_rn(Z[k], e);
                         Q[k] = __ffma2_rn(e, __fmul2_rn(df, df), Q[k]);
                     } else {
@@ -129,8 +135,8 @@ __device__ __forceinline__ void box_energy(const float2 (&ai)[BZ + 2 * D_][(2 + 
                             if (!(vxy1 && vz)) a.y = -FLT_MAX;
                         }
                         const float2 e = make_float2(ex2(a.x), ex2(a.y));
-                        N[k] = __ffma2_rn(e, vw[q + k], N[k]);
-                        Z[k] = __fadd2_rn(Z[k], e);
+                        const float2 v = vw[q + k];
+                        N[k] = __ffma2_rn(e, __fadd2_rn(fi[k], make_float2(-v.x, -v.y)), N[k]);
                     }
                 }
             }
@@ -144,7 +150,6 @@ __device__ __forceinline__ void box_energy(const float2 (&ai)[BZ + 2 * D_][(2 + 
             o3[k] = make_float2(Q[k].x / Z[k].x, Q[k].y / Z[k].y);
         } else {
             o1[k] = N[k];
-            o2[k] = Z[k];
         }
     }
 }
@@ -226,16 +231,15 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, 2, BZ, WY_, WZ_>::NT)
                 const int y = yb + j, z = zb + k;
                 if (y < ny && z < nz) {
                     const long long o = i * nvox + ((long long)z * ny + y) * nx + x;
-                    const float v1 = j == 0 ? o1[k].x : o1[k].y, v2 = j == 0 ? o2[k].x : o2[k].y;
+                    const float v1 = j == 0 ? o1[k].x : o1[k].y;
                     if (PASS == 0) {
-                        const float v3 = j == 0 ? o3[k].x : o3[k].y;
+                        const float v2 = j == 0 ? o2[k].x : o2[k].y, v3 = j == 0 ? o3[k].x : o3[k].y;
                         if (t1) t1[o] = v1;
                         lam[o] = v2;
                         if (qbar) qbar[o] = v3;  // weighted mean of q, for the gradient through the weights
                         jsum += (double)v3;
                     } else {
-                        const float fo = j == 0 ? fi[k].x : fi[k].y;
-                        grad[o] += fo * (1.f + v2) - t1[o] - v1;
+                        grad[o] += t1[o] + v1;
                     }
                 }
             }
