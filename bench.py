@@ -211,9 +211,39 @@ def sweep_ops_per_pair(d: int) -> int:
     return 9 * (2 * d + 1) + 8
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) per clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def measure_compute_peaks(tnlm, stream, gpu_index: int) -> dict:
+    """The compute roofline's denominators measured on this GPU: FP32 FMA
+    (scalar FFMA and packed FP32x2), and ex2, each probe launched alone on
+    8 blocks of 256 threads per SM (8 independent chains per thread) and timed
+    with CUDA events on `stream` (best of 5 after 2 warm-ups), while the SM
+    clock is sampled; the SM count is the device's own."""
+    props = torch.cuda.get_device_properties(gpu_index)
+    sms = int(props.multi_processor_count)
+    blocks = 8 * sms
+    sink = torch.zeros(1, device="cuda")
+    res = {"sms": sms, "device": props.name}
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    for kind, name, iters in ((0, "ffma", 40000), (1, "ffma2", 20000), (2, "ex2", 4000)):
+        ms = []
+        ops = 0.0
+        for rep in range(7):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = tnlm.tnlm_peak_probe(kind, blocks, iters, sink, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if rep >= 2:
+                ms.append(e0.elapsed_time(e1))
+        rate = ops / (min(ms) / 1e3)
+        if kind < 2:
+            res[f"{name}_tflops"] = round(rate / 1e12, 3)
+        else:
+            res["ex2_per_s"] = float(f"{rate:.4g}")
+    res["clocks"] = sampler.stop()
+    res["fp32_tflops"] = max(res["ffma_tflops"], res["ffma2_tflops"])
+    return res
 
 
 def sweep_pairs(cfg):
@@ -298,6 +328,7 @@ def run_ours(args, rank, world, local):
     variants = {} if args.no_variants else measure_variants(tnlm, synth, geom, y, stream, params)
 
     peaks = measured_peaks()
+    cpk = measure_compute_peaks(tnlm, stream, local)
     names = ["k_forward", "k_backproject", "k_sweep"]
     per_launch_ms = {n: stage_ms[k] / max(stage_n[k], 1) for k, n in enumerate(names)}
     abytes = algorithmic_bytes(cfg, geom.proj_shape[0])
@@ -315,14 +346,15 @@ def run_ours(args, rank, world, local):
     nnz = projection_nnz(pb.geom)
     work = {"k_forward": OPS_PER_NNZ_FORWARD * nnz, "k_backproject": OPS_PER_NNZ_BACKPROJECT * nnz,
             "k_sweep": sweep_ops_per_pair(cfg.d) * sweep_pairs(cfg)}
-    peak_t = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    peak_t = cpk["fp32_tflops"]
     alu = {n: {"algorithmic_tflop": round(work[n] / 1e12, 4),
                "achieved_tflops": round(work[n] / (per_launch_ms[n] / 1e3) / 1e12, 3),
                "frac_of_fp32_peak": round(work[n] / (per_launch_ms[n] / 1e3) / 1e12 / peak_t, 4)} for n in names}
     roofline = {"bound": "alu", "kernel": dom, "achieved": alu[dom]["achieved_tflops"], "peak": round(peak_t, 2),
                 "unit": "TFLOP/s", "frac": alu[dom]["frac_of_fp32_peak"], "traffic": traffic,
-                "peak_source": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 FLOP x max SM clock "
-                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peaks['_source']} peaks file)",
+                "peak_source": f"measured FP32 FMA throughput of this GPU ({cpk['sms']} SMs; FFMA "
+                               f"{cpk['ffma_tflops']} and packed FFMA2 {cpk['ffma2_tflops']} TFLOP/s, the larger "
+                               f"taken; SM clock median {cpk['clocks'].get('sm_mhz')} MHz during the probes)",
                 "work": f"{work[dom]:.4g} FP32 ops per launch (nnz(P) = {nnz:.4g})",
                 "hbm_frac": hbm[dom]["frac_of_hbm"]}
     nvox_upd = cfg.n_phases * cfg.vol[0] * cfg.vol[1] * cfg.vol[2]
@@ -346,6 +378,7 @@ def run_ours(args, rank, world, local):
         "stage_ms_per_launch": {n: round(per_launch_ms[n], 4) for n in names},
         "hbm": hbm,
         "alu": alu,
+        "compute_peaks": cpk,
         "roofline": roofline,
         "clocks": clocks,
         # per step: k_forward, the transpose stage (k_colscan + k_backproject_bands on this workload), k_sweep_box
@@ -495,7 +528,7 @@ def batch_configs(n: int = 16, seed: int = 1005):
     return cfgs
 
 
-def measure_batch(tnlm, synth, stream, n_outer: int = 3) -> dict:
+def measure_batch(tnlm, synth, stream, n_outer: int = 20) -> dict:
     """16 uneven problems: sequential tnlm_reconstruct calls against one
     captured plan replayed n_outer times, in FP32 and in BF16 storage, with
     launch shapes tuned per problem first; BF16 error = max over problems of
@@ -505,7 +538,12 @@ def measure_batch(tnlm, synth, stream, n_outer: int = 3) -> dict:
     probs = [synth.recon_problem(c, device="cuda") for c in cfgs]
     geoms = [tnlm.Geometry(pb.geom) for pb in probs]
     ys = [pb.y.contiguous() for pb in probs]
-    params = [tnlm.Params(d=c.d, M=c.M, h=c.h, mu=c.mu, tau=2e-6, n_outer=n_outer) for c in cfgs]
+    taus = []
+    for k, g in enumerate(geoms):  # tau = 1/L per problem (20 power iterations from a seeded start)
+        x0 = torch.from_numpy(synth.uniform(g.vol_shape, 3000 + k)).cuda()
+        taus.append(1.0 / tnlm.tnlm_operator_norm(g, x0, 20))
+        del x0
+    params = [tnlm.Params(d=c.d, M=c.M, h=c.h, mu=c.mu, tau=t, n_outer=n_outer) for c, t in zip(cfgs, taus)]
     for g, p in zip(geoms, params):
         tnlm.tnlm_autotune(g, p)
     fs = [torch.zeros(g.vol_shape, device="cuda") for g in geoms]

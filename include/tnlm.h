@@ -225,8 +225,11 @@ tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int n_phases, const uint16
  *  - the array exists on every GPU that loads the library until the process
  *    exits;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    cudaDeviceReset (or any other teardown of the device's primary
+ *    context) can move the array, and later calls would then write through
+ *    the stale address: do not use this entry point after a device reset;
  *  - every call on a device shares the one array, so calls whose work
  *    overlaps on the GPU (other streams, other host threads) race and give
  *    wrong results: serialise them.  Each sweep overwrites the whole array
@@ -333,6 +336,18 @@ tnlm_status tnlm_operator_norm(tnlm_geometry *geom, float *x, int n_iter, double
  * accumulated milliseconds and launch counts since the last enable. */
 tnlm_status tnlm_set_stage_timing(tnlm_geometry *geom, int enable);
 tnlm_status tnlm_get_stage_timing(const tnlm_geometry *geom, double ms[3], long long launches[3]);
+
+/* Throughput probe for the denominators of the compute roofline (the paper
+ * has no counterpart; a measurement aid).  Launches `blocks` blocks of 256
+ * threads on `stream`; each thread runs 8 independent chains of iters * 8
+ * dependent operations of one kind: 0 = FP32 fused multiply-add, 1 = packed
+ * FP32x2 fused multiply-add, 2 = ex2 of the special-function unit.
+ * *ops_per_launch (HOST) receives the operations of one launch, in FLOP for
+ * kinds 0 and 1 (an FMA counts 2, a packed FMA 4) and in evaluations for
+ * kind 2, so rate = ops / (CUDA-event time of the launch).  sink: one device
+ * float the kernel may write (it never does for the seed used).  Asynchronous;
+ * TNLM_ERR_ARG for an unknown kind, blocks < 1 or iters < 1. */
+tnlm_status tnlm_peak_probe(int kind, int blocks, int iters, float *sink, double *ops_per_launch, void *stream);
 
 const char *tnlm_status_string(tnlm_status status);
 const char *tnlm_last_error(void);

@@ -30,7 +30,7 @@ __all__ = [
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
     "tnlm_energy_grad", "tnlm_energy_grad_weights", "tnlm_energy_grad_bf16", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
-    "reconstruct_host", "library_path",
+    "reconstruct_host", "library_path", "tnlm_peak_probe",
 ]
 
 _lock = threading.Lock()
@@ -133,6 +133,7 @@ def _load():
             "tnlm_set_sweep_shape": (i, [i, i, i, i]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
+            "tnlm_peak_probe": (i, [i, i, i, vp, C.POINTER(C.c_double), vp]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
             "tnlm_status_string": (C.c_char_p, [i]),
             "tnlm_last_error": (C.c_char_p, []),
@@ -396,6 +397,16 @@ def tnlm_enhance_noalloc(g: torch.Tensor, params: Params, out: torch.Tensor, str
     _check(_load().tnlm_enhance_noalloc(nx, ny, nz, np_, _dev(g, "g"), _dev(out, "f", g.device, g.shape),
                                         C.byref(p), _stream(stream)), "tnlm_enhance_noalloc")
     return out
+
+
+def tnlm_peak_probe(kind: int, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launch one throughput probe (0: FP32 FMA, 1: packed FP32x2 FMA, 2: ex2)
+    on `stream`; returns the operations of the launch (FLOP for the FMA
+    kinds, evaluations for ex2).  The caller times it with CUDA events."""
+    ops = C.c_double(0.0)
+    _check(_load().tnlm_peak_probe(int(kind), int(blocks), int(iters), _dev(sink, "sink"), C.byref(ops),
+                                   _stream(stream)), "tnlm_peak_probe")
+    return float(ops.value)
 
 
 def tnlm_cgls(geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, report: bool = False, stream=None):
