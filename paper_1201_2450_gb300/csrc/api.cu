@@ -459,10 +459,6 @@ static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnl
 
 }  // namespace tnlm
 
-extern "C" {
-
-}  // extern "C"
-
 template <class T>
 static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, double *report,
                                  void *stream)
