@@ -349,6 +349,14 @@ tnlm_status tnlm_get_stage_timing(const tnlm_geometry *geom, double ms[3], long 
  * TNLM_ERR_ARG for an unknown kind, blocks < 1 or iters < 1. */
 tnlm_status tnlm_peak_probe(int kind, int blocks, int iters, float *sink, double *ops_per_launch, void *stream);
 
+/* Test hook for the out-of-memory paths (no counterpart in the paper): the
+ * next `count` device allocations the library attempts (workspaces of a
+ * geometry handle, the ping-pong images of TNLM-E, the weight-gradient
+ * workspace) fail as if the device were out of memory, so the call returns
+ * TNLM_ERR_OOM before it launches anything; a later call allocates normally
+ * and the handle stays usable.  0 disables; process-wide. */
+tnlm_status tnlm_test_fail_allocations(int count);
+
 const char *tnlm_status_string(tnlm_status status);
 const char *tnlm_last_error(void);
 int tnlm_version(void); /* major * 10000 + minor * 100 + patch */

@@ -134,6 +134,7 @@ def _load():
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_peak_probe": (i, [i, i, i, vp, C.POINTER(C.c_double), vp]),
+            "tnlm_test_fail_allocations": (i, [i]),
             "tnlm_get_stage_timing": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
             "tnlm_status_string": (C.c_char_p, [i]),
             "tnlm_last_error": (C.c_char_p, []),

@@ -2,6 +2,7 @@
 // loops of TNLM-R and TNLM-E (Sec. 2.3) and the power iteration.  Every
 // arithmetic step runs in the kernels of projector.cu, tnlm_sweep.cu and
 // reduce.cu; this file only orders launches on the caller's stream.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -34,11 +35,25 @@ static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// Test hook of the out-of-memory paths: while positive, each device
+// allocation the library attempts fails as if the device were full.
+static std::atomic<int> g_forced_alloc_failures{0};
+
+static bool forced_alloc_failure()
+{
+    int n = g_forced_alloc_failures.load();
+    while (n > 0) {
+        if (g_forced_alloc_failures.compare_exchange_weak(n, n - 1)) return true;
+    }
+    return false;
+}
+
 template <class T>
 static tnlm_status dev_alloc(T **p, size_t count)
 {
     if (*p) return TNLM_OK;
-    if (cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+    if (forced_alloc_failure() ||
+        cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         set_error("cudaMalloc of %zu bytes for the workspace failed", sizeof(T) * count);
@@ -98,8 +113,9 @@ float *prefix_workspace(tnlm_geometry *g)
 {
     if (!bands_apply(g->kg)) return nullptr;
     if (!g->d_pref) {
-        if (cudaMalloc(reinterpret_cast<void **>(&g->d_pref), sizeof(float) * prefix_floats(g->kg, g->n_views_total)) !=
-            cudaSuccess) {
+        if (forced_alloc_failure() ||
+            cudaMalloc(reinterpret_cast<void **>(&g->d_pref), sizeof(float) * prefix_floats(g->kg, g->n_views_total)) !=
+                cudaSuccess) {
             cudaGetLastError();
             g->d_pref = nullptr;
         }
@@ -196,6 +212,13 @@ const char *tnlm_status_string(tnlm_status s)
 const char *tnlm_last_error(void) { return g_last_error; }
 
 int tnlm_version(void) { return 10000; }
+
+tnlm_status tnlm_test_fail_allocations(int count)
+{
+    if (count < 0) return arg_error("count must be >= 0");
+    g_forced_alloc_failures.store(count);
+    return TNLM_OK;
+}
 
 tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry **out)
 {
@@ -659,7 +682,7 @@ tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *
     }
     float *tmp = nullptr;
     if (p->n_outer > 1) {
-        if (cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(float) * n, st) != cudaSuccess) {
+        if (forced_alloc_failure() || cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(float) * n, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMallocAsync of the ping-pong buffer (%zu bytes) failed", sizeof(float) * n);
             return TNLM_ERR_OOM;
@@ -702,7 +725,8 @@ tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int np, const uint16_t *g,
     }
     uint16_t *tmp = nullptr;
     if (p->n_outer > 1) {
-        if (cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint16_t) * n, st) != cudaSuccess) {
+        if (forced_alloc_failure() ||
+            cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint16_t) * n, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMallocAsync of the BF16 ping-pong buffer (%zu bytes) failed", sizeof(uint16_t) * n);
             return TNLM_ERR_OOM;
@@ -833,7 +857,7 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int np, const float
     cudaStream_t st = as_stream(stream);
     const size_t n = energy_weights_grad_floats(nx, ny, nz, np, d, M);
     float *ws = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), sizeof(float) * n, st) != cudaSuccess) {
+    if (forced_alloc_failure() || cudaMallocAsync(reinterpret_cast<void **>(&ws), sizeof(float) * n, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMallocAsync of %zu bytes for the weight-gradient workspace failed", sizeof(float) * n);
         return TNLM_ERR_OOM;

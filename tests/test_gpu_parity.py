@@ -976,3 +976,64 @@ def test_batch_plan_bf16_equals_single_calls():
     torch.cuda.synchronize()
     for a, b in zip(single, fb):
         assert torch.equal(a, b)
+
+
+def test_out_of_memory_paths_and_recovery(ora):
+    """Device allocations made to fail on the host (the library's test hook,
+    no GPU fault): tnlm_reconstruct and tnlm_enhance return 'out of device
+    memory' before launching anything and the same handle then works and
+    gives the normal result; a failed transpose prefix workspace falls back
+    to the exact per-cell transpose, still equal to the oracle."""
+    lib = tnlm._load()
+    pb = synth.recon_problem(synth.C1)
+    p = tnlm.Params(d=1, M=2, h=0.02, mu=1.0, tau=1e-3, n_outer=2)
+    G = tnlm.Geometry(pb.geom)
+    f = torch.zeros(G.vol_shape, device="cuda")
+    assert lib.tnlm_test_fail_allocations(1) == 0
+    with pytest.raises(tnlm.TnlmError) as e:
+        tnlm.tnlm_reconstruct(G, cuda(pb.y.numpy()), f, p)
+    assert e.value.status == 3 and "failed" in str(e.value)
+    assert torch.count_nonzero(f) == 0
+    tnlm.tnlm_reconstruct(G, cuda(pb.y.numpy()), f, p)
+    G2 = tnlm.Geometry(pb.geom)
+    f2 = torch.zeros(G2.vol_shape, device="cuda")
+    tnlm.tnlm_reconstruct(G2, cuda(pb.y.numpy()), f2, p)
+    torch.cuda.synchronize()
+    assert torch.equal(f, f2)
+    g = cuda(synth.smooth_volume((3, 8, 12, 16), 5))
+    pe = tnlm.Params(d=1, M=1, h=0.02, mu=1.0, n_outer=3, clip_nonneg=0)
+    assert lib.tnlm_test_fail_allocations(1) == 0
+    with pytest.raises(tnlm.TnlmError) as e:
+        tnlm.tnlm_enhance(g, pe)
+    assert e.value.status == 3
+    ref = ora.enhance(g.cpu().numpy(), 1, 1, 0.02, 1.0, 3)
+    assert rel_l2(tnlm.tnlm_enhance(g, pe).cpu().numpy(), ref) <= RTOL
+    # transpose without its prefix workspace: the exact per-cell form
+    geom = GEOMS["ragged_uneven"]
+    G3 = tnlm.Geometry(geom)
+    proj = synth.uniform(G3.proj_shape, 77)
+    assert lib.tnlm_test_fail_allocations(1) == 0
+    bt = tnlm.tnlm_backproject(G3, cuda(proj)).cpu().numpy()
+    assert lib.tnlm_test_fail_allocations(0) == 0
+    assert rel_l2(bt, ora.backproject(ora.Geometry(geom), proj)) <= RTOL
+    for h in (G, G2, G3):
+        h.close()
+
+
+def test_reconstruct_resumes_from_its_iterate():
+    """TNLM-R keeps no state between iterations besides f (the weights are
+    recomputed from g^(k) every iteration), so resuming from a saved iterate
+    is a second call: 3 + 2 iterations equal 5 bit for bit."""
+    pb = synth.recon_problem(synth.C1)
+    y = cuda(pb.y.numpy())
+    G = tnlm.Geometry(pb.geom)
+    f5 = torch.zeros(G.vol_shape, device="cuda")
+    tnlm.tnlm_reconstruct(G, y, f5, tnlm.Params(d=1, M=2, h=0.02, mu=1.0, tau=1e-3, n_outer=5))
+    f = torch.zeros(G.vol_shape, device="cuda")
+    tnlm.tnlm_reconstruct(G, y, f, tnlm.Params(d=1, M=2, h=0.02, mu=1.0, tau=1e-3, n_outer=3))
+    saved = f.cpu()
+    f = saved.cuda()
+    tnlm.tnlm_reconstruct(G, y, f, tnlm.Params(d=1, M=2, h=0.02, mu=1.0, tau=1e-3, n_outer=2))
+    torch.cuda.synchronize()
+    assert torch.equal(f, f5)
+    G.close()
