@@ -64,7 +64,8 @@ typedef struct {
     double du, dv;           /* pixel pitch, mm (> 0) */
     double u_off, v_off;     /* detector centre offset along u and v, mm */
     double sad, sdd;         /* source-isocentre and source-detector distances, mm (sdd > sad > 0) */
-    int n_phases;            /* N_p >= 2 */
+    int n_phases;            /* N_p >= 1 (the TNLM calls need N_p >= 2; one phase serves projection, and a
+                                rank's share of the phases in the sharded form) */
     const int *n_views;      /* host array [n_phases], each >= 1 */
     const double *angles_rad;/* host array [sum n_views], phase-major view angles */
 } tnlm_geometry_desc;
@@ -137,6 +138,30 @@ tnlm_status tnlm_weights(int nx, int ny, int nz, int n_phases, const float *wsrc
 tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float *wsrc, const float *vals,
                               const float *g, float *f_out, int d, int M, float h, float mu, int clip,
                               void *stream);
+
+/* One Gauss-Jacobi sweep of Eq. 8, as tnlm_gauss_jacobi, for the output
+ * phases p0 .. p0 + n_out - 1 only, of arrays ([n_phases][nz][ny][nx]) of
+ * n_phases phases whose ring neighbours are (i +- 1) mod n_phases.  The
+ * phase-sharded form of TNLM-R / TNLM-E (each process owning a contiguous
+ * block of the N_p phases; Eq. 8 couples phase i to i +- 1 only) sweeps its
+ * own phases 1 .. n_loc of arrays of n_loc + 2 phases whose first and last
+ * phases hold the neighbours' edge phases (halos); for N_p = 2 split over
+ * two processes both halos are the other phase, as in the literal periodic
+ * reading.  Phases outside the range of f_out are not written.  TNLM_ERR_ARG
+ * if the range leaves [0, n_phases) or as tnlm_gauss_jacobi. */
+tnlm_status tnlm_gauss_jacobi_range(int nx, int ny, int nz, int n_phases, int p0, int n_out, const float *wsrc,
+                                    const float *vals, const float *g, float *f_out, int d, int M, float h, float mu,
+                                    int clip, void *stream);
+
+/* Step 1 of one FBS iteration of TNLM-R (Sec. 2.3), problem (P1) alone:
+ * g = the result of params->n_inner gradient steps g <- g - tau P^T (P g - y)
+ * (or CGLS iterations, p1_solver = 1) started at f, for every phase of the
+ * handle (the phases are uncoupled in (P1)).  f, g: [N_p][nz][ny][nx]
+ * (distinct); y: [sum n_views][nv][nu].  report (HOST, nullable) receives
+ * ||P g - y||^2 before each of the n_inner steps and makes the call
+ * synchronise `stream`.  Uses the handle's workspace as tnlm_reconstruct. */
+tnlm_status tnlm_p1(tnlm_geometry *geom, const float *y, const float *f, float *g, const tnlm_params *params,
+                    double *report, void *stream);
 
 /* TNLM-R (Sec. 2.3): f holds f^(0) on entry and f^(n_outer) on exit.  Each
  * FBS iteration k: (P1) from g = f^(k-1) by n_inner gradient steps

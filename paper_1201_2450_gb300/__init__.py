@@ -30,7 +30,7 @@ __all__ = [
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
     "tnlm_energy_grad", "tnlm_energy_grad_weights", "tnlm_energy_grad_bf16", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
-    "reconstruct_host", "library_path", "tnlm_peak_probe",
+    "reconstruct_host", "library_path", "tnlm_peak_probe", "tnlm_gauss_jacobi_range", "tnlm_p1",
 ]
 
 _lock = threading.Lock()
@@ -109,6 +109,8 @@ def _load():
             "tnlm_backproject": (i, [vp, vp, vp, f, f, vp]),
             "tnlm_weights": (i, [i, i, i, i, vp, i, i, f, vp, sz, vp]),
             "tnlm_gauss_jacobi": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_gauss_jacobi_range": (i, [i, i, i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_p1": (i, [vp, vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_enhance_noalloc": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
@@ -276,6 +278,31 @@ def tnlm_gauss_jacobi(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d
                                      _dev(g, "g", dev, wsrc.shape), _dev(out, "f_out", dev, wsrc.shape), d, M, h,
                                      mu, int(clip), _stream(stream)), "tnlm_gauss_jacobi")
     return out
+
+
+def tnlm_gauss_jacobi_range(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, out: torch.Tensor, p0: int,
+                            n_out: int, d: int, M: int, h: float, mu: float, clip: int = 0, stream=None):
+    """One Eq. 8 sweep of the output phases p0 .. p0 + n_out - 1 of arrays of
+    wsrc.shape[0] phases (ring neighbours (i +- 1) mod that count) into out."""
+    np_, nz, ny, nx = wsrc.shape
+    dev = wsrc.device
+    _check(_load().tnlm_gauss_jacobi_range(nx, ny, nz, np_, int(p0), int(n_out), _dev(wsrc, "wsrc"),
+                                           _dev(vals, "vals", dev, wsrc.shape), _dev(g, "g", dev, wsrc.shape),
+                                           _dev(out, "f_out", dev, wsrc.shape), d, M, h, mu, int(clip),
+                                           _stream(stream)), "tnlm_gauss_jacobi_range")
+    return out
+
+
+def tnlm_p1(geom: Geometry, y: torch.Tensor, f: torch.Tensor, g: torch.Tensor, params: Params, report: bool = False,
+            stream=None):
+    """(P1) of one FBS iteration from f into g (params.n_inner gradient steps or
+    CGLS iterations); returns the residual norms before each step, or None."""
+    rep = np.zeros(params.n_inner, np.float64) if report else None
+    p = params._c()
+    _check(_load().tnlm_p1(geom.handle, _dev(y, "y", geom.device, geom.proj_shape),
+                           _dev(f, "f", geom.device, geom.vol_shape), _dev(g, "g", geom.device, geom.vol_shape),
+                           C.byref(p), rep.ctypes.data if rep is not None else None, _stream(stream)), "tnlm_p1")
+    return rep
 
 
 def tnlm_reconstruct(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: Params, report: bool = False,

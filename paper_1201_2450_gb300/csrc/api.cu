@@ -236,7 +236,7 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry *
         !std::isfinite(d.cz))
         return arg_error("offsets must be finite");
     if (!finite_pos(d.sad) || !finite_pos(d.sdd) || !(d.sdd > d.sad)) return arg_error("need 0 < sad < sdd");
-    if (d.n_phases < 2) return arg_error("n_phases must be >= 2 (N_p = 1 would compare a phase with itself)");
+    if (d.n_phases < 1) return arg_error("n_phases must be >= 1");  // the TNLM calls themselves need N_p >= 2
     if (!d.n_views || !d.angles_rad) return arg_error("n_views and angles_rad must not be NULL");
     long long total = 0;
     for (int i = 0; i < d.n_phases; ++i) {
@@ -434,19 +434,19 @@ static tnlm_status sweep_t(const KGeom &kg, const uint16_t *wsrc, const uint16_t
 // One FBS iteration k of TNLM-R (Sec. 2.3) on stream st; timer may be null.
 // T = float (FP32 storage) or uint16_t (BF16 storage: y, f, g and the sweep
 // scratch hold BF16; projections of the residual and every sum stay FP32).
+// Step 1 of an FBS iteration k, (P1) from f^(k-1) into g: CGLS (the paper's solver) or n_inner
+// gradient steps.  report: the residual norms go to the handle's scalars (slots of iteration k).
 template <class T>
-static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, int k, bool report,
-                                 StageTimer *timer, cudaStream_t st)
+static tnlm_status p1_step(tnlm_geometry *geo, const T *y, const T *f, T *g, const tnlm_params *p, int k,
+                           bool report, StageTimer *timer, cudaStream_t st)
 {
     const KGeom &kg = geo->kg;
     const long long nblk = forward_blocks(kg, geo->n_views_total);
-    T *g = reinterpret_cast<T *>(geo->d_g), *tmp = reinterpret_cast<T *>(geo->d_tmp);
-    // step 1: (P1) from f^(k-1): CGLS (the paper's solver) or n_inner gradient steps
     if constexpr (std::is_same<T, float>::value) {
         if (p->p1_solver == 1) {
             if (timer) timer->begin(0);
-            TNLM_TRY_CUDA(cudaMemcpyAsync(geo->d_g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
-            TNLM_TRY(run_cgls(cgls_args(geo, y, geo->d_g, p->n_inner,
+            TNLM_TRY_CUDA(cudaMemcpyAsync(g, f, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToDevice, st));
+            TNLM_TRY(run_cgls(cgls_args(geo, y, g, p->n_inner,
                                         report ? geo->d_scalars + (long long)k * (p->n_inner + 1) : nullptr),
                               st));
             if (timer) timer->end();
@@ -463,6 +463,16 @@ static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnl
                                     prefix_workspace(geo), geo->n_views_total, st));
         if (timer) timer->end();
     }
+    return TNLM_OK;
+}
+
+template <class T>
+static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, int k, bool report,
+                                 StageTimer *timer, cudaStream_t st)
+{
+    const KGeom &kg = geo->kg;
+    T *g = reinterpret_cast<T *>(geo->d_g), *tmp = reinterpret_cast<T *>(geo->d_tmp);
+    TNLM_TRY(p1_step<T>(geo, y, f, g, p, k, report, timer, st));
     // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
     if (timer) timer->begin(2);
     const int ngj = p->n_gj > 0 ? p->n_gj : 1;
@@ -666,6 +676,43 @@ tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const flo
     const tnlm_status st = tnlm_batch_plan_run(plan, n_outer, stream);
     tnlm_batch_plan_destroy(plan);
     return st;
+}
+
+tnlm_status tnlm_gauss_jacobi_range(int nx, int ny, int nz, int np, int p0, int n_out, const float *wsrc,
+                                    const float *vals, const float *g, float *f_out, int d, int M, float h, float mu,
+                                    int clip, void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, mu));
+    if (!wsrc || !vals || !g || !f_out) return arg_error("wsrc, vals, g and f_out must not be NULL");
+    if (f_out == wsrc || f_out == vals || f_out == g) return arg_error("f_out must not alias wsrc, vals or g");
+    if (p0 < 0 || n_out < 1 || (long long)p0 + n_out > np) {
+        set_error("output phases [%d, %d) must lie inside the %d phases of the arrays", p0, p0 + n_out, np);
+        return TNLM_ERR_ARG;
+    }
+    return launch_sweep_range(nx, ny, nz, np, p0, n_out, wsrc, vals, g, f_out, d, M, h, mu, clip, as_stream(stream));
+}
+
+tnlm_status tnlm_p1(tnlm_geometry *geo, const float *y, const float *f, float *g, const tnlm_params *p,
+                    double *report, void *stream)
+{
+    if (!g) return arg_error("g must not be NULL");
+    if (!p) return arg_error("params must not be NULL");
+    if (g == f) return arg_error("g must not alias f");
+    if (!geo || !y || !f) return arg_error("geometry, y and f must not be NULL");
+    TNLM_TRY(check_params(p, true));
+    const long long n_slots = p->p1_solver == 1 ? p->n_inner + 1 : p->n_inner;
+    TNLM_TRY(ensure_workspace(geo, false, n_slots));
+    if (p->p1_solver == 1) TNLM_TRY(ensure_cgls_workspace(geo));
+    prefix_workspace(geo);
+    cudaStream_t st = as_stream(stream);
+    TNLM_TRY(p1_step<float>(geo, y, f, g, p, 0, report != nullptr, nullptr, st));
+    if (report) {
+        std::vector<double> tmp((size_t)n_slots);
+        TNLM_TRY_CUDA(cudaMemcpyAsync(tmp.data(), geo->d_scalars, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, st));
+        TNLM_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int t = 0; t < p->n_inner; ++t) report[t] = tmp[(size_t)t];
+    }
+    return TNLM_OK;
 }
 
 tnlm_status tnlm_enhance(int nx, int ny, int nz, int np, const float *g, float *f, const tnlm_params *p, void *stream)

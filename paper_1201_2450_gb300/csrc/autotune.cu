@@ -209,7 +209,8 @@ tnlm_status tnlm_autotune(tnlm_geometry *geo, const tnlm_params *p, int *choice,
     const float c2 = exponent_scale(p->h);
     TNLM_TRY(tune_sweep<float>(
         [&](int s, cudaError_t *err) {
-            return launch_box_shape(s, p->d, p->M, kg.nx, kg.ny, kg.nz, kg.np, f, f, f, geo->d_g, c2, p->mu, 1, st, err);
+            return launch_box_shape(s, p->d, p->M, kg.nx, kg.ny, kg.nz, kg.np, 0, kg.np, f, f, f, geo->d_g, c2, p->mu, 1, st,
+                                    err);
         },
         tm, st, &v));
     if (v >= 0) set_box_shape(p->d, p->M, 0, v);
@@ -241,7 +242,7 @@ tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int np, int d, int M, fl
         TNLM_TRY(fill_bf16(a, n, 0x4321u, 0.04f, st));
         TNLM_TRY(tune_sweep<uint16_t>(
             [&](int s, cudaError_t *err) {
-                return launch_box_shape_bf16(s, d, M, nx, ny, nz, np, a, a, a, o, c2, 1.0f, 0, st, err);
+                return launch_box_shape_bf16(s, d, M, nx, ny, nz, np, 0, np, a, a, a, o, c2, 1.0f, 0, st, err);
             },
             tm, st, &v));
     } else {
@@ -249,7 +250,7 @@ tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int np, int d, int M, fl
         TNLM_TRY(fill(a, n, 0x4321u, 0.04f, st));
         TNLM_TRY(tune_sweep<float>(
             [&](int s, cudaError_t *err) {
-                return launch_box_shape(s, d, M, nx, ny, nz, np, a, a, a, o, c2, 1.0f, 0, st, err);
+                return launch_box_shape(s, d, M, nx, ny, nz, np, 0, np, a, a, a, o, c2, 1.0f, 0, st, err);
             },
             tm, st, &v));
     }

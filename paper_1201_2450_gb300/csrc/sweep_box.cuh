@@ -238,7 +238,7 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
 
 template <int D_, int M_, int BY, int BZ, int WY_, int WZ_, class T>
 __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
-    k_sweep_box(int nx, int ny, int nz, int np, int ntx, int nty, int ntz, const T *__restrict__ wsrc,
+    k_sweep_box(int nx, int ny, int nz, int np, int p0, int ntx, int nty, int ntz, const T *__restrict__ wsrc,
                 const T *__restrict__ vals, const T *__restrict__ g, T *__restrict__ out, float c2,
                 float mu, int clip)
 {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
     const int ty_i = b % nty;
     b /= nty;
     const int tz_i = b % ntz;
-    const int i = b / ntz;
+    const int i = p0 + b / ntz;  // output phase (ring neighbours (i +- 1) mod np)
     const int X0 = tx_i * C::TXO, Y0 = ty_i * C::TY, Z0 = tz_i * C::TZ;
     const int x = X0 - D_ + lane;
     const int yb = Y0 + wy * BY, zb = Z0 + wz * BZ;
@@ -311,19 +311,20 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
     }
 }
 
+// phases p0 .. p0 + nout - 1 of arrays of np phases
 template <int D_, int M_, int BZ, int WY_, int WZ_, class T>
-bool launch_box(int nx, int ny, int nz, int np, const T *wsrc, const T *vals, const T *g, T *out,
+bool launch_box(int nx, int ny, int nz, int np, int p0, int nout, const T *wsrc, const T *vals, const T *g, T *out,
                 float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
 {
     constexpr int BY = 2;
     using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
     const int ntx = (nx + C::TXO - 1) / C::TXO, nty = (ny + C::TY - 1) / C::TY, ntz = (nz + C::TZ - 1) / C::TZ;
-    const long long blocks = (long long)ntx * nty * ntz * np;
+    const long long blocks = (long long)ntx * nty * ntz * nout;
     if (blocks > 0x7fffffffLL) return false;
     auto kern = k_sweep_box<D_, M_, BY, BZ, WY_, WZ_, T>;
     *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (*err != cudaSuccess) return true;
-    kern<<<(unsigned)blocks, C::NT, C::SMEM, st>>>(nx, ny, nz, np, ntx, nty, ntz, wsrc, vals, g, out, c2, mu, clip);
+    kern<<<(unsigned)blocks, C::NT, C::SMEM, st>>>(nx, ny, nz, np, p0, ntx, nty, ntz, wsrc, vals, g, out, c2, mu, clip);
     *err = cudaGetLastError();
     return true;
 }
@@ -338,13 +339,14 @@ template <> struct BoxShape<3> { static constexpr int WY = 8, WZ = 2, BZ = 2; };
 
 // (d, M) dispatch of one launch shape; false when (d, M) has no box kernel
 template <int V, class T>
-bool launch_shape(int d, int M, int nx, int ny, int nz, int np, const T *wsrc, const T *vals, const T *g, T *out,
-                  float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
+bool launch_shape(int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const T *wsrc, const T *vals,
+                  const T *g, T *out, float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
 {
     using S = BoxShape<V>;
 #define TNLM_BOX_CASE(DD, MM)                                                                                   \
     if (d == DD && M == MM)                                                                                      \
-        return launch_box<DD, MM, S::BZ, S::WY, S::WZ, T>(nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
+        return launch_box<DD, MM, S::BZ, S::WY, S::WZ, T>(nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, \
+                                                          st, err);
     TNLM_BOX_CASE(1, 1)
     TNLM_BOX_CASE(1, 2)
     TNLM_BOX_CASE(1, 3)
@@ -361,18 +363,19 @@ bool launch_shape(int d, int M, int nx, int ny, int nz, int np, const T *wsrc, c
 // Defines the two entry points of launch shape V (FP32 and BF16 storage).
 #define TNLM_BOX_VARIANT_TU(V)                                                                                    \
     namespace tnlm {                                                                                              \
-    bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,    \
-                           const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,            \
-                           cudaError_t *err)                                                                      \
+    bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,     \
+                           const float *vals, const float *g, float *out, float c2, float mu, int clip,          \
+                           cudaStream_t st, cudaError_t *err)                                                     \
     {                                                                                                             \
-        return box::launch_shape<V, float>(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);   \
+        return box::launch_shape<V, float>(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st,  \
+                                           err);                                                                  \
     }                                                                                                             \
-    bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,           \
-                                  const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu,     \
-                                  int clip, cudaStream_t st, cudaError_t *err)                                    \
+    bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                \
+                                  const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out,   \
+                                  float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)                \
     {                                                                                                             \
         using B = __nv_bfloat16;                                                                                  \
-        return box::launch_shape<V, B>(d, M, nx, ny, nz, np, reinterpret_cast<const B *>(wsrc),                 \
+        return box::launch_shape<V, B>(d, M, nx, ny, nz, np, p0, nout, reinterpret_cast<const B *>(wsrc),       \
                                        reinterpret_cast<const B *>(vals), reinterpret_cast<const B *>(g),         \
                                        reinterpret_cast<B *>(out), c2, mu, clip, st, err);                        \
     }                                                                                                             \

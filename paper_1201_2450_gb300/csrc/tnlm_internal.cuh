@@ -82,6 +82,12 @@ size_t prefix_floats(const KGeom &kg, int n_views_total);
 
 tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
                          float *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
+// the sweep for output phases p0 .. p0 + nout - 1 of arrays of np phases (ring neighbours (i +- 1) mod np)
+tnlm_status launch_sweep_range(int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc, const float *vals,
+                               const float *g, float *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
+tnlm_status launch_sweep_range_bf16(int nx, int ny, int nz, int np, int p0, int nout, const uint16_t *wsrc,
+                                    const uint16_t *vals, const uint16_t *g, uint16_t *out, int d, int M, float h,
+                                    float mu, int clip, cudaStream_t st);
 tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,
                            cudaStream_t st);
 // BF16 images (bit patterns), FP32 arithmetic; box configurations only
@@ -157,18 +163,19 @@ tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float
 constexpr int kBoxShapes = 4;
 int box_shape(int d, int M, int bf16);
 void set_box_shape(int d, int M, int bf16, int v);
-bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,
-                      const float *g, float *out, float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);
-bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,
-                           const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu, int clip,
-                           cudaStream_t st, cudaError_t *err);
+bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,
+                      const float *vals, const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,
+                      cudaError_t *err);
+bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout,
+                           const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2,
+                           float mu, int clip, cudaStream_t st, cudaError_t *err);
 #define TNLM_BOX_DECL(V)                                                                                          \
-    bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,    \
-                           const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,            \
-                           cudaError_t *err);                                                                     \
-    bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,           \
-                                  const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu,     \
-                                  int clip, cudaStream_t st, cudaError_t *err);
+    bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,     \
+                           const float *vals, const float *g, float *out, float c2, float mu, int clip,          \
+                           cudaStream_t st, cudaError_t *err);                                                    \
+    bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                \
+                                  const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out,   \
+                                  float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);
 TNLM_BOX_DECL(0)
 TNLM_BOX_DECL(1)
 TNLM_BOX_DECL(2)

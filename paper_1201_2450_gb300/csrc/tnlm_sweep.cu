@@ -48,7 +48,7 @@ __device__ __forceinline__ void stage_clamped(float *dst, const float *__restric
 }
 
 __global__ void __launch_bounds__(kTX *kTY *kTZ)
-    k_sweep(int nx, int ny, int nz, int np, int ntz, const float *__restrict__ wsrc, const float *__restrict__ vals,
+    k_sweep(int nx, int ny, int nz, int np, int p0, int ntz, const float *__restrict__ wsrc, const float *__restrict__ vals,
             const float *__restrict__ g, float *__restrict__ out, int d, int M, float c2, float mu, int clip)
 {
     extern __shared__ float sm[];
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kTX *kTY *kTZ)
 
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int tid = (tz * kTY + ty) * kTX + tx;
-    const int i = blockIdx.z / ntz;
+    const int i = p0 + blockIdx.z / ntz;  // output phase (ring neighbours (i +- 1) mod np)
     const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, Z0 = (blockIdx.z % ntz) * kTZ;
     const long long nvox = (long long)nx * ny * nz;
     const int x = X0 + tx, y = Y0 + ty, z = Z0 + tz;
@@ -194,26 +194,27 @@ void set_box_shape(int d, int M, int bf16, int v)
     g_box_shape[d][M][bf16 ? 1 : 0] = v;
 }
 
-bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,
-                      const float *g, float *out, float c2, float mu, int clip, cudaStream_t st, cudaError_t *err)
+bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,
+                      const float *vals, const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,
+                      cudaError_t *err)
 {
     switch (v) {
-    case 1: return launch_box_var1(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    case 2: return launch_box_var2(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    case 3: return launch_box_var3(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    default: return launch_box_var0(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 1: return launch_box_var1(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 2: return launch_box_var2(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 3: return launch_box_var3(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    default: return launch_box_var0(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
     }
 }
 
-bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, const uint16_t *wsrc,
-                           const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2, float mu, int clip,
-                           cudaStream_t st, cudaError_t *err)
+bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout,
+                           const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2,
+                           float mu, int clip, cudaStream_t st, cudaError_t *err)
 {
     switch (v) {
-    case 1: return launch_box_var1_bf16(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    case 2: return launch_box_var2_bf16(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    case 3: return launch_box_var3_bf16(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
-    default: return launch_box_var0_bf16(d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 1: return launch_box_var1_bf16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 2: return launch_box_var2_bf16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 3: return launch_box_var3_bf16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    default: return launch_box_var0_bf16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
     }
 }
 
@@ -257,13 +258,17 @@ static float exponent_scale(float h)
     return (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
 }
 
-tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
-                         float *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
+tnlm_status launch_sweep_range(int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc, const float *vals,
+                               const float *g, float *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
 {
+    if (p0 < 0 || nout < 1 || p0 + nout > np) {
+        set_error("output phases [%d, %d) must lie in [0, %d)", p0, p0 + nout, np);
+        return TNLM_ERR_ARG;
+    }
     const float c2 = exponent_scale(h);
     cudaError_t err = cudaSuccess;
-    const bool done = launch_box_shape(box_shape(d, M, 0), d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip, st,
-                                       &err);
+    const bool done = launch_box_shape(box_shape(d, M, 0), d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu,
+                                       clip, st, &err);
     if (done) {
         if (err != cudaSuccess) {
             set_error("box-sum sweep launch failed: %s", cudaGetErrorString(err));
@@ -274,22 +279,33 @@ tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, cons
     // other (d, M): generic tiled kernel with direct patch sums
     const int ntz = (nz + kTZ - 1) / kTZ;
     dim3 block(kTX, kTY, kTZ);
-    dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, np * ntz);
+    dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, nout * ntz);
     const size_t smem = sweep_smem(d, M);
     if (smem > 48 * 1024)
         TNLM_TRY_CUDA(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sweep<<<grid, block, smem, st>>>(nx, ny, nz, np, ntz, wsrc, vals, g, out, d, M, c2, mu, clip);
+    k_sweep<<<grid, block, smem, st>>>(nx, ny, nz, np, p0, ntz, wsrc, vals, g, out, d, M, c2, mu, clip);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
 }
 
-tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
-                              const uint16_t *g, uint16_t *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
+tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, const float *vals, const float *g,
+                         float *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
 {
+    return launch_sweep_range(nx, ny, nz, np, 0, np, wsrc, vals, g, out, d, M, h, mu, clip, st);
+}
+
+tnlm_status launch_sweep_range_bf16(int nx, int ny, int nz, int np, int p0, int nout, const uint16_t *wsrc,
+                                    const uint16_t *vals, const uint16_t *g, uint16_t *out, int d, int M, float h,
+                                    float mu, int clip, cudaStream_t st)
+{
+    if (p0 < 0 || nout < 1 || p0 + nout > np) {
+        set_error("output phases [%d, %d) must lie in [0, %d)", p0, p0 + nout, np);
+        return TNLM_ERR_ARG;
+    }
     const float c2 = exponent_scale(h);
     cudaError_t err = cudaSuccess;
-    const bool done = launch_box_shape_bf16(box_shape(d, M, 1), d, M, nx, ny, nz, np, wsrc, vals, g, out, c2, mu, clip,
-                                            st, &err);
+    const bool done = launch_box_shape_bf16(box_shape(d, M, 1), d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2,
+                                            mu, clip, st, &err);
     if (!done) {
         set_error("BF16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", d, M);
         return TNLM_ERR_NOT_IMPLEMENTED;
@@ -299,6 +315,12 @@ tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *ws
         return TNLM_ERR_CUDA;
     }
     return TNLM_OK;
+}
+
+tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
+                              const uint16_t *g, uint16_t *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
+{
+    return launch_sweep_range_bf16(nx, ny, nz, np, 0, np, wsrc, vals, g, out, d, M, h, mu, clip, st);
 }
 
 tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,

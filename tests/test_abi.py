@@ -54,7 +54,7 @@ def _desc(**over):
     (dict(nx=0), "volume dimensions"),
     (dict(dx=-1.0), "voxel sizes"),
     (dict(sdd=900.0), "sad < sdd"),
-    (dict(nviews=np.array([3], np.int32), angles=np.zeros(3)), "n_phases"),
+    (dict(nviews=np.array([], np.int32), angles=np.zeros(0)), "n_phases"),
     (dict(nviews=np.array([3, 0], np.int32), angles=np.zeros(3)), "at least one view"),
     (dict(nx=2000, dx=1.0), "inside the source circle"),
     (dict(nv=7000), "nv must not exceed"),
@@ -75,6 +75,15 @@ def test_sweep_argument_checks(lib):
     assert lib.tnlm_gauss_jacobi(4, 4, 4, 2, vp, vp, vp, C.c_void_p(32), 1, 1, 0.0, 1.0, 0, None) == 1
     assert lib.tnlm_gauss_jacobi(4, 4, 4, 2, vp, vp, vp, vp, 1, 1, 0.1, 1.0, 0, None) == 1  # aliasing
     assert b"alias" in lib.tnlm_last_error()
+    # the range sweep: output phases must lie inside the arrays' phases
+    assert lib.tnlm_gauss_jacobi_range(4, 4, 4, 3, 1, 3, vp, vp, vp, C.c_void_p(32), 1, 1, 0.1, 1.0, 0, None) == 1
+    assert b"must lie inside" in lib.tnlm_last_error()
+    assert lib.tnlm_gauss_jacobi_range(4, 4, 4, 3, -1, 1, vp, vp, vp, C.c_void_p(32), 1, 1, 0.1, 1.0, 0, None) == 1
+    assert lib.tnlm_gauss_jacobi_range(4, 4, 4, 3, 1, 1, vp, vp, vp, vp, 1, 1, 0.1, 1.0, 0, None) == 1  # aliasing
+    assert b"alias" in lib.tnlm_last_error()
+    # (P1) alone: null and aliased arguments are rejected before any device work
+    assert lib.tnlm_p1(None, vp, vp, C.c_void_p(32), None, None, None) == 1
+    assert lib.tnlm_p1(vp, vp, vp, vp, None, None, None) == 1
     # weight buffer too small
     assert lib.tnlm_weights(4, 4, 4, 2, vp, 1, 1, 0.1, vp, 10, None) == 1
     assert b"needed" in lib.tnlm_last_error()
