@@ -437,13 +437,26 @@ def measure_variants(tnlm, synth, geom, y, stream, params) -> dict:
         f32.zero_()
         tnlm.tnlm_reconstruct(geom, y, f32, p3)
 
+    yh = y.half()
+    fh = torch.zeros(geom.vol_shape, device="cuda", dtype=torch.float16)
+
+    def rh():
+        fh.zero_()
+        tnlm.tnlm_reconstruct_fp16(geom, yh, fh, p3)
+
     ms16 = _time_ms(r16, stream)
+    msh = _time_ms(rh, stream)
     ms32 = _time_ms(r32, stream)
+
+    def rel(a):
+        return float(f"{float(torch.linalg.vector_norm((a.float() - f32).double()) / torch.linalg.vector_norm(f32.double())):.3e}")
+
     out["bf16_recon_ms_per_iteration"] = round(ms16 / 3, 3)
+    out["fp16_recon_ms_per_iteration"] = round(msh / 3, 3)
     out["fp32_recon_ms_per_iteration_same_run"] = round(ms32 / 3, 3)
-    out["bf16_recon_rel_l2_vs_fp32_3_iterations"] = float(
-        f"{float(torch.linalg.vector_norm((f16.float() - f32).double()) / torch.linalg.vector_norm(f32.double())):.3e}")
-    del y16, f16, f32
+    out["bf16_recon_rel_l2_vs_fp32_3_iterations"] = rel(f16)
+    out["fp16_recon_rel_l2_vs_fp32_3_iterations"] = rel(fh)
+    del y16, f16, f32, yh, fh
     c3 = synth.C3
     g, _ = synth.enhance_input(c3, device="cuda")
     f = torch.empty_like(g)
@@ -461,7 +474,13 @@ def measure_variants(tnlm, synth, geom, y, stream, params) -> dict:
     bf_ms = _time_ms(lambda: tnlm.tnlm_enhance_bf16(gb, p, out=fb), stream, reps=2)
     out["tnlm_e_bf16_ms_per_sweep"] = round(bf_ms, 3)
     out["tnlm_e_bf16_voxel_updates_per_s"] = round(nvox / (bf_ms / 1e3), 1)
-    del g, f, gb, fb
+    out["tnlm_e_fp16_sweep_shape"] = tnlm.tnlm_autotune_sweep(tuple(g.shape), c3.d, c3.M, c3.h, fp16=True)
+    gh = g.half()
+    fhh = torch.empty_like(gh)
+    h_ms = _time_ms(lambda: tnlm.tnlm_enhance_fp16(gh, p, out=fhh), stream, reps=2)
+    out["tnlm_e_fp16_ms_per_sweep"] = round(h_ms, 3)
+    out["tnlm_e_fp16_voxel_updates_per_s"] = round(nvox / (h_ms / 1e3), 1)
+    del g, f, gb, fb, gh, fhh
     torch.cuda.empty_cache()
     # differentiable total energy (frozen weights) on 10 x 128^3, 40 views x 256x192
     c4 = synth.C4

@@ -189,6 +189,14 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, cons
 tnlm_status tnlm_reconstruct_bf16(tnlm_geometry *geom, const uint16_t *y, uint16_t *f, const tnlm_params *params,
                                   double *report, void *stream);
 
+/* The same with IEEE half-precision storage (FP16 bit patterns: 11-bit
+ * significands, eight times finer than bfloat16, ample range for
+ * attenuation values and line integrals); every rule of
+ * tnlm_reconstruct_bf16 applies, outputs round to nearest FP16.  The *_fp16
+ * calls below are the FP16 forms of the corresponding *_bf16 calls. */
+tnlm_status tnlm_reconstruct_fp16(tnlm_geometry *geom, const uint16_t *y, uint16_t *f, const tnlm_params *params,
+                                  double *report, void *stream);
+
 /* TNLM-R for a batch of independent problems (uneven sizes, phase counts
  * and view counts allowed) in one CUDA graph: one FBS iteration of every
  * problem is captured (problems on parallel graph branches) and the graph
@@ -216,6 +224,8 @@ tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *s
 /* The same plan for problems stored in BF16 (as tnlm_reconstruct_bf16). */
 tnlm_status tnlm_batch_plan_create_bf16(int n_problems, tnlm_geometry *const *geoms, const uint16_t *const *y,
                                         uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out);
+tnlm_status tnlm_batch_plan_create_fp16(int n_problems, tnlm_geometry *const *geoms, const uint16_t *const *y,
+                                        uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out);
 void tnlm_batch_plan_destroy(tnlm_batch_plan *plan);
 
 /* TNLM-E (Sec. 2.3): f^(0) = g, then params->n_outer sweeps of (weights of
@@ -236,6 +246,11 @@ tnlm_status tnlm_gauss_jacobi_bf16(int nx, int ny, int nz, int n_phases, const u
                                    const uint16_t *g, uint16_t *f_out, int d, int M, float h, float mu, int clip,
                                    void *stream);
 tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int n_phases, const uint16_t *g, uint16_t *f,
+                              const tnlm_params *params, void *stream);
+tnlm_status tnlm_gauss_jacobi_fp16(int nx, int ny, int nz, int n_phases, const uint16_t *wsrc, const uint16_t *vals,
+                                   const uint16_t *g, uint16_t *f_out, int d, int M, float h, float mu, int clip,
+                                   void *stream);
+tnlm_status tnlm_enhance_fp16(int nx, int ny, int nz, int n_phases, const uint16_t *g, uint16_t *f,
                               const tnlm_params *params, void *stream);
 
 /* TNLM-E without any device allocation, for callers that cannot allocate
@@ -290,6 +305,8 @@ tnlm_status tnlm_energy_grad(tnlm_geometry *geom, const float *y, const float *f
  * {1,2,3} (TNLM_ERR_NOT_IMPLEMENTED otherwise). */
 tnlm_status tnlm_energy_grad_bf16(tnlm_geometry *geom, const uint16_t *y, const uint16_t *f, const uint16_t *a,
                                   const tnlm_params *params, double *energy, float *grad, void *stream);
+tnlm_status tnlm_energy_grad_fp16(tnlm_geometry *geom, const uint16_t *y, const uint16_t *f, const uint16_t *a,
+                                  const tnlm_params *params, double *energy, float *grad, void *stream);
 
 /* Gradient of the TNLM half of the energy, 1/2 sum_i J[f_i, f_{i+1}] (J of
  * Eq. 2 over the search window, direction-0 weights of Eq. 9 computed from
@@ -323,8 +340,9 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * rows, sweep shape} to choice[4] (nullable).  It synchronises `stream` and
  * uses the handle's workspace, so call it before capturing a graph and not
  * while other calls on the handle are queued.
- * tnlm_autotune_sweep does the same for the sweep alone (bf16 != 0: the BF16
- * storage kernels), writing the chosen shape to *shape (nullable).
+ * tnlm_autotune_sweep does the same for the sweep alone (bf16 = 1: the BF16
+ * storage kernels, 2: the FP16 ones; the argument of tnlm_set_sweep_shape
+ * likewise), writing the chosen shape to *shape (nullable).
  * tnlm_set_launch_shapes / tnlm_set_sweep_shape set a shape directly
  * (TNLM_ERR_ARG for a shape that is not compiled).  The sweep-shape table
  * is shared by the whole process: change it from one host thread at a time

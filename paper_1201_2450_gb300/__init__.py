@@ -31,6 +31,7 @@ __all__ = [
     "tnlm_energy_grad", "tnlm_energy_grad_weights", "tnlm_energy_grad_bf16", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path", "tnlm_peak_probe", "tnlm_gauss_jacobi_range", "tnlm_p1",
+    "tnlm_reconstruct_fp16", "tnlm_enhance_fp16", "tnlm_gauss_jacobi_fp16", "tnlm_energy_grad_fp16",
 ]
 
 _lock = threading.Lock()
@@ -134,6 +135,12 @@ def _load():
             "tnlm_set_launch_shapes": (i, [vp, i, i, i]),
             "tnlm_set_sweep_shape": (i, [i, i, i, i]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
+            "tnlm_enhance_fp16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
+            "tnlm_gauss_jacobi_fp16": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_energy_grad_fp16": (i, [vp, vp, vp, vp, C.POINTER(_Params), C.POINTER(C.c_double), vp, vp]),
+            "tnlm_batch_plan_create_fp16": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(_Params),
+                                                C.POINTER(vp)]),
+            "tnlm_reconstruct_fp16": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_set_stage_timing": (i, [vp, i]),
             "tnlm_peak_probe": (i, [i, i, i, vp, C.POINTER(C.c_double), vp]),
             "tnlm_test_fail_allocations": (i, [i]),
@@ -336,17 +343,27 @@ def tnlm_reconstruct_batch(geoms, ys, fs, params, stream=None):
     return fs
 
 
+def _reconstruct16(name, dtype, geom, y, f, params, report, stream):
+    rep = np.zeros((params.n_outer, params.n_inner), np.float64) if report else None
+    p = params._c()
+    _check(getattr(_load(), name)(geom.handle, _dev(y, "y", geom.device, geom.proj_shape, dtype),
+                                  _dev(f, "f", geom.device, geom.vol_shape, dtype), C.byref(p),
+                                  rep.ctypes.data if rep is not None else None, _stream(stream)), name)
+    return f, rep
+
+
 def tnlm_reconstruct_bf16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: Params, report: bool = False,
                           stream=None):
     """TNLM-R in place on bfloat16 f from bfloat16 y, FP32 arithmetic;
     returns (f, report or None)."""
-    rep = np.zeros((params.n_outer, params.n_inner), np.float64) if report else None
-    p = params._c()
-    _check(_load().tnlm_reconstruct_bf16(geom.handle, _dev(y, "y", geom.device, geom.proj_shape, torch.bfloat16),
-                                         _dev(f, "f", geom.device, geom.vol_shape, torch.bfloat16), C.byref(p),
-                                         rep.ctypes.data if rep is not None else None, _stream(stream)),
-           "tnlm_reconstruct_bf16")
-    return f, rep
+    return _reconstruct16("tnlm_reconstruct_bf16", torch.bfloat16, geom, y, f, params, report, stream)
+
+
+def tnlm_reconstruct_fp16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, params: Params, report: bool = False,
+                          stream=None):
+    """TNLM-R in place on float16 f from float16 y, FP32 arithmetic;
+    returns (f, report or None)."""
+    return _reconstruct16("tnlm_reconstruct_fp16", torch.float16, geom, y, f, params, report, stream)
 
 
 def tnlm_autotune(geom: Geometry, params: Params, stream=None) -> dict:
@@ -359,11 +376,16 @@ def tnlm_autotune(geom: Geometry, params: Params, stream=None) -> dict:
     return {"projector_rows": out[0], "transpose_cells": out[1], "transpose_rows": out[2], "sweep_shape": out[3]}
 
 
-def tnlm_autotune_sweep(shape, d: int, M: int, h: float, bf16: bool = False, stream=None) -> int:
-    """Tune the box-sum sweep for a [N_p, nz, ny, nx] problem; returns the shape index."""
+def _storage(bf16, fp16) -> int:
+    return 2 if fp16 else (1 if bf16 else 0)
+
+
+def tnlm_autotune_sweep(shape, d: int, M: int, h: float, bf16: bool = False, stream=None, fp16: bool = False) -> int:
+    """Tune the box-sum sweep for a [N_p, nz, ny, nx] problem (FP32, BF16 or
+    FP16 storage); returns the shape index."""
     np_, nz, ny, nx = shape
     out = C.c_int()
-    _check(_load().tnlm_autotune_sweep(nx, ny, nz, np_, d, M, h, int(bool(bf16)), C.byref(out), _stream(stream)),
+    _check(_load().tnlm_autotune_sweep(nx, ny, nz, np_, d, M, h, _storage(bf16, fp16), C.byref(out), _stream(stream)),
            "tnlm_autotune_sweep")
     return out.value
 
@@ -373,8 +395,8 @@ def tnlm_set_launch_shapes(geom: Geometry, projector_rows: int, transpose_cells:
            "tnlm_set_launch_shapes")
 
 
-def tnlm_set_sweep_shape(d: int, M: int, bf16: bool, shape: int):
-    _check(_load().tnlm_set_sweep_shape(d, M, int(bool(bf16)), shape), "tnlm_set_sweep_shape")
+def tnlm_set_sweep_shape(d: int, M: int, bf16: bool, shape: int, fp16: bool = False):
+    _check(_load().tnlm_set_sweep_shape(d, M, _storage(bf16, fp16), shape), "tnlm_set_sweep_shape")
 
 
 class BatchPlan:
@@ -383,11 +405,12 @@ class BatchPlan:
     references to the geometries and tensors it was built on."""
 
     def __init__(self, geoms, ys, fs, params):
-        bf16 = len(fs) > 0 and fs[0].dtype == torch.bfloat16
-        n, G, Y, F, P = _batch_args(geoms, ys, fs, params, torch.bfloat16 if bf16 else torch.float32)
+        dtype = fs[0].dtype if len(fs) > 0 else torch.float32
+        n, G, Y, F, P = _batch_args(geoms, ys, fs, params, dtype)
         self._keep = (list(geoms), list(ys), list(fs))
         self.handle = C.c_void_p()
-        create = _load().tnlm_batch_plan_create_bf16 if bf16 else _load().tnlm_batch_plan_create
+        create = {torch.bfloat16: _load().tnlm_batch_plan_create_bf16,
+                  torch.float16: _load().tnlm_batch_plan_create_fp16}.get(dtype, _load().tnlm_batch_plan_create)
         _check(create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
 
     def run(self, n_iterations: int, stream=None):
@@ -469,6 +492,32 @@ def tnlm_gauss_jacobi_bf16(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tens
     return out
 
 
+def tnlm_gauss_jacobi_fp16(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d: int, M: int, h: float,
+                           mu: float, clip: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One Eq. 8 sweep on float16 images with FP32 arithmetic."""
+    np_, nz, ny, nx = wsrc.shape
+    if out is None:
+        out = torch.empty_like(wsrc)
+    hf, dev = torch.float16, wsrc.device
+    _check(_load().tnlm_gauss_jacobi_fp16(nx, ny, nz, np_, _dev(wsrc, "wsrc", dtype=hf),
+                                          _dev(vals, "vals", dev, wsrc.shape, hf), _dev(g, "g", dev, wsrc.shape, hf),
+                                          _dev(out, "f_out", dev, wsrc.shape, hf), d, M, h, mu, int(clip),
+                                          _stream(stream)), "tnlm_gauss_jacobi_fp16")
+    return out
+
+
+def tnlm_enhance_fp16(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """TNLM-E on float16 images with FP32 arithmetic."""
+    np_, nz, ny, nx = g.shape
+    if out is None:
+        out = torch.empty_like(g)
+    p = params._c()
+    hf = torch.float16
+    _check(_load().tnlm_enhance_fp16(nx, ny, nz, np_, _dev(g, "g", dtype=hf), _dev(out, "f", g.device, g.shape, hf),
+                                     C.byref(p), _stream(stream)), "tnlm_enhance_fp16")
+    return out
+
+
 def tnlm_enhance_bf16(g: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """TNLM-E on bfloat16 images with FP32 arithmetic."""
     np_, nz, ny, nx = g.shape
@@ -508,6 +557,22 @@ def tnlm_energy_grad_bf16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: t
                                          _dev(a, "a", geom.device, geom.vol_shape, b), C.byref(p), C.byref(E),
                                          _dev(grad, "grad", geom.device, geom.vol_shape), _stream(stream)),
            "tnlm_energy_grad_bf16")
+    return E.value, grad
+
+
+def tnlm_energy_grad_fp16(geom: Geometry, y: torch.Tensor, f: torch.Tensor, a: torch.Tensor, params: Params,
+                          grad: torch.Tensor | None = None, stream=None):
+    """tnlm_energy_grad on float16 y, f and a; the gradient is FP32."""
+    if grad is None:
+        grad = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
+    E = C.c_double()
+    p = params._c()
+    hf = torch.float16
+    _check(_load().tnlm_energy_grad_fp16(geom.handle, _dev(y, "y", geom.device, geom.proj_shape, hf),
+                                         _dev(f, "f", geom.device, geom.vol_shape, hf),
+                                         _dev(a, "a", geom.device, geom.vol_shape, hf), C.byref(p), C.byref(E),
+                                         _dev(grad, "grad", geom.device, geom.vol_shape), _stream(stream)),
+           "tnlm_energy_grad_fp16")
     return E.value, grad
 
 

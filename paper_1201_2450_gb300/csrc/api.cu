@@ -401,14 +401,14 @@ static tnlm_status prepare_reconstruct(tnlm_geometry *geo, const void *y, const 
     TNLM_TRY(check_params(p, true));
     const KGeom &kg = geo->kg;
     TNLM_TRY(check_sweep_args(kg.nx, kg.ny, kg.nz, kg.np, p->d, p->M, p->h, p->mu));
-    if (bf16) {
+    if (bf16) {  // 16-bit storage (BF16 or FP16)
         if (p->p1_solver == 1) {
-            set_error("BF16 storage runs (P1) as gradient steps only (p1_solver = 0)");
+            set_error("16-bit storage runs (P1) as gradient steps only (p1_solver = 0)");
             return TNLM_ERR_NOT_IMPLEMENTED;
         }
         const bool box = (p->d == 1 || p->d == 2) && p->M >= 1 && p->M <= 3;
         if (!box) {
-            set_error("BF16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", p->d, p->M);
+            set_error("16-bit storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", p->d, p->M);
             return TNLM_ERR_NOT_IMPLEMENTED;
         }
     }
@@ -431,9 +431,17 @@ static tnlm_status sweep_t(const KGeom &kg, const uint16_t *wsrc, const uint16_t
     return launch_sweep_bf16(kg.nx, kg.ny, kg.nz, kg.np, wsrc, vals, g, out, p->d, p->M, p->h, p->mu, clip, st);
 }
 
+static tnlm_status sweep_t(const KGeom &kg, const __half *wsrc, const __half *vals, const __half *g, __half *out,
+                           const tnlm_params *p, int clip, cudaStream_t st)
+{
+    return launch_sweep_range_f16(kg.nx, kg.ny, kg.nz, kg.np, 0, kg.np, wsrc, vals, g, out, p->d, p->M, p->h, p->mu,
+                                  clip, st);
+}
+
 // One FBS iteration k of TNLM-R (Sec. 2.3) on stream st; timer may be null.
-// T = float (FP32 storage) or uint16_t (BF16 storage: y, f, g and the sweep
-// scratch hold BF16; projections of the residual and every sum stay FP32).
+// T = float (FP32 storage), uint16_t (BF16 storage) or __half (FP16 storage):
+// with 16-bit storage y, f, g and the sweep scratch are 16-bit; projections of
+// the residual and every sum stay FP32.
 // Step 1 of an FBS iteration k, (P1) from f^(k-1) into g: CGLS (the paper's solver) or n_inner
 // gradient steps.  report: the residual norms go to the handle's scalars (slots of iteration k).
 template <class T>
@@ -499,7 +507,7 @@ static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnl
     if (!p) return arg_error("params must not be NULL");
     const long long n_norms = (long long)p->n_outer * p->n_inner;
     const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
-    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots, std::is_same<T, uint16_t>::value));
+    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots, !std::is_same<T, float>::value));
     cudaStream_t st = as_stream(stream);
     StageTimer timer(geo, st);
     for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration<T>(geo, y, f, p, k, report != nullptr, &timer, st));
@@ -532,6 +540,13 @@ tnlm_status tnlm_reconstruct_bf16(tnlm_geometry *geo, const uint16_t *y, uint16_
     return reconstruct_t<uint16_t>(geo, y, f, p, report, stream);
 }
 
+tnlm_status tnlm_reconstruct_fp16(tnlm_geometry *geo, const uint16_t *y, uint16_t *f, const tnlm_params *p,
+                                  double *report, void *stream)
+{
+    return reconstruct_t<__half>(geo, reinterpret_cast<const __half *>(y), reinterpret_cast<__half *>(f), p, report,
+                                 stream);
+}
+
 struct tnlm_batch_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -550,7 +565,7 @@ static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const T *co
     for (int b = 0; b < n; ++b) {
         for (int c = 0; c < b; ++c)
             if (geoms[c] == geoms[b]) return arg_error("a geometry handle may appear once per batch (it owns the workspace)");
-        TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1, std::is_same<T, uint16_t>::value));
+        TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1, !std::is_same<T, float>::value));
     }
     const int ns = n < 8 ? n : 8;  // parallel branches of the graph
     cudaStream_t cs = nullptr;
@@ -639,6 +654,13 @@ tnlm_status tnlm_batch_plan_create_bf16(int n, tnlm_geometry *const *geoms, cons
                                         uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out)
 {
     return plan_create<uint16_t>(n, geoms, y, f, params, out);
+}
+
+tnlm_status tnlm_batch_plan_create_fp16(int n, tnlm_geometry *const *geoms, const uint16_t *const *y,
+                                        uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out)
+{
+    return plan_create<__half>(n, geoms, reinterpret_cast<const __half *const *>(y),
+                               reinterpret_cast<__half *const *>(f), params, out);
 }
 
 tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream)
@@ -757,37 +779,75 @@ tnlm_status tnlm_gauss_jacobi_bf16(int nx, int ny, int nz, int np, const uint16_
     return launch_sweep_bf16(nx, ny, nz, np, wsrc, vals, g, f_out, d, M, h, mu, clip, as_stream(stream));
 }
 
-tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int np, const uint16_t *g, uint16_t *f, const tnlm_params *p,
-                              void *stream)
+tnlm_status tnlm_gauss_jacobi_fp16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
+                                   const uint16_t *g, uint16_t *f_out, int d, int M, float h, float mu, int clip,
+                                   void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, mu));
+    if (!wsrc || !vals || !g || !f_out) return arg_error("wsrc, vals, g and f_out must not be NULL");
+    if (f_out == wsrc || f_out == vals || f_out == g) return arg_error("f_out must not alias wsrc, vals or g");
+    using H = __half;
+    return launch_sweep_range_f16(nx, ny, nz, np, 0, np, reinterpret_cast<const H *>(wsrc),
+                                  reinterpret_cast<const H *>(vals), reinterpret_cast<const H *>(g),
+                                  reinterpret_cast<H *>(f_out), d, M, h, mu, clip, as_stream(stream));
+}
+
+}  // extern "C"
+
+// TNLM-E with 16-bit storage (T = uint16_t: BF16 bit patterns, T = __half: FP16)
+template <class T>
+static tnlm_status enhance16_t(int nx, int ny, int nz, int np, const T *g, T *f, const tnlm_params *p, void *stream)
 {
     TNLM_TRY(check_params(p, false));
     TNLM_TRY(check_sweep_args(nx, ny, nz, np, p->d, p->M, p->h, p->mu));
     if (!g || !f) return arg_error("g and f must not be NULL");
-    if (g == f) return arg_error("g and f must not alias");
+    if ((const void *)g == (const void *)f) return arg_error("g and f must not alias");
     cudaStream_t st = as_stream(stream);
     const size_t n = (size_t)np * nx * ny * nz;
     if (p->n_outer == 0) {
-        TNLM_TRY_CUDA(cudaMemcpyAsync(f, g, sizeof(uint16_t) * n, cudaMemcpyDeviceToDevice, st));
+        TNLM_TRY_CUDA(cudaMemcpyAsync(f, g, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
         return TNLM_OK;
     }
-    uint16_t *tmp = nullptr;
+    T *tmp = nullptr;
     if (p->n_outer > 1) {
-        if (forced_alloc_failure() ||
-            cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint16_t) * n, st) != cudaSuccess) {
+        if (forced_alloc_failure() || cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(T) * n, st) != cudaSuccess) {
             cudaGetLastError();
-            set_error("cudaMallocAsync of the BF16 ping-pong buffer (%zu bytes) failed", sizeof(uint16_t) * n);
+            set_error("cudaMallocAsync of the 16-bit ping-pong buffer (%zu bytes) failed", sizeof(T) * n);
             return TNLM_ERR_OOM;
         }
     }
-    const uint16_t *src = g;
+    const KGeom kg = [&] {
+        KGeom k{};
+        k.nx = nx;
+        k.ny = ny;
+        k.nz = nz;
+        k.np = np;
+        return k;
+    }();
+    const T *src = g;
     tnlm_status s = TNLM_OK;
     for (int k = 0; k < p->n_outer && s == TNLM_OK; ++k) {
-        uint16_t *dst = ((p->n_outer - 1 - k) % 2 == 0) ? f : tmp;
-        s = launch_sweep_bf16(nx, ny, nz, np, src, src, g, dst, p->d, p->M, p->h, p->mu, p->clip_nonneg, st);
+        T *dst = ((p->n_outer - 1 - k) % 2 == 0) ? f : tmp;
+        s = sweep_t(kg, src, src, g, dst, p, p->clip_nonneg, st);
         src = dst;
     }
     if (tmp) cudaFreeAsync(tmp, st);
     return s;
+}
+
+extern "C" {
+
+tnlm_status tnlm_enhance_bf16(int nx, int ny, int nz, int np, const uint16_t *g, uint16_t *f, const tnlm_params *p,
+                              void *stream)
+{
+    return enhance16_t<uint16_t>(nx, ny, nz, np, g, f, p, stream);
+}
+
+tnlm_status tnlm_enhance_fp16(int nx, int ny, int nz, int np, const uint16_t *g, uint16_t *f, const tnlm_params *p,
+                              void *stream)
+{
+    return enhance16_t<__half>(nx, ny, nz, np, reinterpret_cast<const __half *>(g), reinterpret_cast<__half *>(f), p,
+                               stream);
 }
 
 tnlm_status tnlm_operator_norm(tnlm_geometry *geo, float *x, int n_iter, double *L_out, void *stream)
@@ -834,6 +894,19 @@ static tnlm_status energy_tnlm_t(const KGeom &kg, const float *a, const float *f
                                  float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st)
 {
     return launch_energy_tnlm(kg.nx, kg.ny, kg.nz, kg.np, a, f, p->d, p->M, p->h, lam, t1, grad, jpart, nblk, st);
+}
+
+static tnlm_status energy_tnlm_t(const KGeom &kg, const __half *a, const __half *f, const tnlm_params *p,
+                                 float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st)
+{
+    cudaError_t err = cudaSuccess;
+    if (!launch_energy_box_f16(p->d, p->M, kg.nx, kg.ny, kg.nz, kg.np, a, f, p->h, lam, t1, grad, jpart, nblk, st,
+                               &err)) {
+        set_error("FP16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", p->d, p->M);
+        return TNLM_ERR_NOT_IMPLEMENTED;
+    }
+    TNLM_TRY_CUDA(err);
+    return TNLM_OK;
 }
 
 static tnlm_status energy_tnlm_t(const KGeom &kg, const uint16_t *a, const uint16_t *f, const tnlm_params *p,
@@ -893,6 +966,14 @@ tnlm_status tnlm_energy_grad_bf16(tnlm_geometry *geo, const uint16_t *y, const u
                                   const tnlm_params *p, double *energy, float *grad, void *stream)
 {
     return energy_grad_t<uint16_t>(geo, y, f, a, p, energy, grad, stream);
+}
+
+tnlm_status tnlm_energy_grad_fp16(tnlm_geometry *geo, const uint16_t *y, const uint16_t *f, const uint16_t *a,
+                                  const tnlm_params *p, double *energy, float *grad, void *stream)
+{
+    using H = __half;
+    return energy_grad_t<H>(geo, reinterpret_cast<const H *>(y), reinterpret_cast<const H *>(f),
+                            reinterpret_cast<const H *>(a), p, energy, grad, stream);
 }
 
 tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int np, const float *f, const float *a, int d, int M,

@@ -36,6 +36,12 @@ __global__ void k_fill_hash_bf16(uint16_t *__restrict__ x, long long n, uint32_t
     }
 }
 
+__global__ void k_fill_hash_f16(__half *__restrict__ x, long long n, uint32_t seed, float scale)
+{
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        x[t] = __float2half_rn(scale * (float)(mix32((uint32_t)t ^ seed) >> 8) * (1.0f / 16777216.0f));
+}
+
 tnlm_status fill(float *x, long long n, uint32_t seed, float scale, cudaStream_t st)
 {
     k_fill_hash<<<1024, 256, 0, st>>>(x, n, seed, scale);
@@ -229,7 +235,7 @@ tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int np, int d, int M, fl
     TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, 1.0f));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const long long n = (long long)np * nx * ny * nz;
-    const size_t es = bf16 ? sizeof(uint16_t) : sizeof(float);
+    const size_t es = bf16 ? sizeof(uint16_t) : sizeof(float);  // bf16: the storage kind (1 BF16, 2 FP16)
     Scratch sa(st), so(st);
     TNLM_TRY(sa.alloc(es * n));
     TNLM_TRY(so.alloc(es * n));
@@ -237,7 +243,16 @@ tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int np, int d, int M, fl
     TNLM_TRY(tm.init());
     const float c2 = exponent_scale(h);
     int v = -1;
-    if (bf16) {
+    if (bf16 == 2) {
+        __half *a = static_cast<__half *>(sa.p), *o = static_cast<__half *>(so.p);
+        k_fill_hash_f16<<<1024, 256, 0, st>>>(a, n, 0x4321u, 0.04f);
+        TNLM_TRY_CUDA(cudaGetLastError());
+        TNLM_TRY(tune_sweep<__half>(
+            [&](int s, cudaError_t *err) {
+                return launch_box_shape_f16(s, d, M, nx, ny, nz, np, 0, np, a, a, a, o, c2, 1.0f, 0, st, err);
+            },
+            tm, st, &v));
+    } else if (bf16) {
         uint16_t *a = static_cast<uint16_t *>(sa.p), *o = static_cast<uint16_t *>(so.p);
         TNLM_TRY(fill_bf16(a, n, 0x4321u, 0.04f, st));
         TNLM_TRY(tune_sweep<uint16_t>(

@@ -521,6 +521,14 @@ bool launch_energy_weights_grad_box(int d, int M, int nx, int ny, int nz, int np
     return false;
 }
 
+bool launch_energy_box_f16(int d, int M, int nx, int ny, int nz, int np, const __half *a, const __half *f,
+                           float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
+                           cudaStream_t st, cudaError_t *err)
+{
+    const float c2 = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    return box::launch_energy<__half>(d, M, nx, ny, nz, np, a, f, c2, lam, t1, grad, jpart, nblk, st, err);
+}
+
 bool launch_energy_box_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *a, const uint16_t *f,
                             float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
                             cudaStream_t st, cudaError_t *err)

@@ -13,6 +13,7 @@
 // (isocentre plane for the projector, the voxel column for the transpose)
 // so that FP32 positions keep ~1e-5 voxel resolution.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cfloat>
 #include <cmath>
@@ -30,10 +31,13 @@ constexpr int kBpBX = 32, kBpBY = 4, kBpCH = 8;  // exact transpose block: 32 x 
 // on load (every sum stays FP32; a BF16 output is rounded once).
 __device__ __forceinline__ float ldg_v(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ldg_v(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float ldg_v(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ float ld_v(const float *p) { return *p; }
 __device__ __forceinline__ float ld_v(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld_v(const __half *p) { return __half2float(*p); }
 __device__ __forceinline__ void st_v(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_v(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st_v(__half *p, float v) { *p = __float2half_rn(v); }
 
 // Enter the slab 0 <= E + b G < n (voxel-index units) into [blo, bhi];
 // a ray parallel to the slab is inside iff 0 <= E < n (half-open cells).
@@ -612,6 +616,12 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
                                reinterpret_cast<const B *>(y), out, partials, mode, st);
 }
 
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const __half *vol,
+                           const __half *y, float *out, double *partials, int mode, cudaStream_t st)
+{
+    return launch_forward_t<__half>(kg, views, n_views_total, vol, y, out, partials, mode, st);
+}
+
 bool bands_apply(const KGeom &kg)
 {
     // a ray's chord through one voxel column rises by at most |v|max / SDD per mm of horizontal path,
@@ -703,6 +713,14 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
     using B = __nv_bfloat16;
     return launch_backproject_t<B>(kg, views, view_off, proj, reinterpret_cast<const B *>(vin),
                                    reinterpret_cast<B *>(vout), alpha, beta, scaled, pref_ws, n_views_total, st);
+}
+
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const __half *vin, __half *vout, float alpha, float beta, bool scaled,
+                               float *pref_ws, int n_views_total, cudaStream_t st)
+{
+    return launch_backproject_t<__half>(kg, views, view_off, proj, vin, vout, alpha, beta, scaled, pref_ws,
+                                        n_views_total, st);
 }
 
 }  // namespace tnlm

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cfloat>
 #include <cmath>
@@ -31,8 +32,10 @@ __device__ __forceinline__ int clampi(int a, int n) { return a < 0 ? 0 : (a >= n
 
 __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 
 template <class T>
 __device__ __forceinline__ void stage_clamped(float *dst, const T *__restrict__ src, int ox, int oy, int oz,
@@ -378,5 +381,12 @@ bool launch_shape(int d, int M, int nx, int ny, int nz, int np, int p0, int nout
         return box::launch_shape<V, B>(d, M, nx, ny, nz, np, p0, nout, reinterpret_cast<const B *>(wsrc),       \
                                        reinterpret_cast<const B *>(vals), reinterpret_cast<const B *>(g),         \
                                        reinterpret_cast<B *>(out), c2, mu, clip, st, err);                        \
+    }                                                                                                             \
+    bool launch_box_var##V##_f16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                 \
+                                 const __half *wsrc, const __half *vals, const __half *g, __half *out, float c2,  \
+                                 float mu, int clip, cudaStream_t st, cudaError_t *err)                           \
+    {                                                                                                             \
+        return box::launch_shape<V, __half>(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, \
+                                            err);                                                                 \
     }                                                                                                             \
     }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libtnlm.so.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -63,6 +64,9 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
 // BF16 storage of vol and y (bit patterns), FP32 arithmetic and FP32 output
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const uint16_t *vol,
                            const uint16_t *y, float *out, double *partials, int mode, cudaStream_t st);
+// FP16 storage of vol and y, FP32 arithmetic and FP32 output
+tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const __half *vol,
+                           const __half *y, float *out, double *partials, int mode, cudaStream_t st);
 long long forward_blocks(const KGeom &kg, int n_views_total);
 long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
 
@@ -77,6 +81,10 @@ tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int
 tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
                                const uint16_t *vin, uint16_t *vout, float alpha, float beta, bool scaled,
                                float *pref_ws, int n_views_total, cudaStream_t st);
+// FP16 storage of vin / vout; proj stays FP32
+tnlm_status launch_backproject(const KGeom &kg, const ViewGeom *views, const int *view_off, const float *proj,
+                               const __half *vin, __half *vout, float alpha, float beta, bool scaled,
+                               float *pref_ws, int n_views_total, cudaStream_t st);
 bool bands_apply(const KGeom &kg);
 size_t prefix_floats(const KGeom &kg, int n_views_total);
 
@@ -88,6 +96,10 @@ tnlm_status launch_sweep_range(int nx, int ny, int nz, int np, int p0, int nout,
 tnlm_status launch_sweep_range_bf16(int nx, int ny, int nz, int np, int p0, int nout, const uint16_t *wsrc,
                                     const uint16_t *vals, const uint16_t *g, uint16_t *out, int d, int M, float h,
                                     float mu, int clip, cudaStream_t st);
+// FP16 images, FP32 arithmetic; box configurations only
+tnlm_status launch_sweep_range_f16(int nx, int ny, int nz, int np, int p0, int nout, const __half *wsrc,
+                                   const __half *vals, const __half *g, __half *out, int d, int M, float h, float mu,
+                                   int clip, cudaStream_t st);
 tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,
                            cudaStream_t st);
 // BF16 images (bit patterns), FP32 arithmetic; box configurations only
@@ -145,6 +157,9 @@ long long energy_box_blocks(int nx, int ny, int nz, int np);
 bool launch_energy_box(int d, int M, int nx, int ny, int nz, int np, const float *a, const float *f, float h,
                        float *lam, float *t1, float *grad, double *jpart, long long *nblk, cudaStream_t st,
                        cudaError_t *err);
+bool launch_energy_box_f16(int d, int M, int nx, int ny, int nz, int np, const __half *a, const __half *f,
+                           float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
+                           cudaStream_t st, cudaError_t *err);
 bool launch_energy_box_bf16(int d, int M, int nx, int ny, int nz, int np, const uint16_t *a, const uint16_t *f,
                             float h, float *lam, float *t1, float *grad, double *jpart, long long *nblk,
                             cudaStream_t st, cudaError_t *err);
@@ -161,21 +176,28 @@ tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float
 // has no box kernel.  box_shape / set_box_shape hold the process-wide choice
 // per (d, M, storage) that tnlm_autotune makes.
 constexpr int kBoxShapes = 4;
-int box_shape(int d, int M, int bf16);
-void set_box_shape(int d, int M, int bf16, int v);
+// storage: 0 FP32, 1 BF16, 2 FP16 (a nonzero value other than 2 reads as BF16)
+int box_shape(int d, int M, int storage);
+void set_box_shape(int d, int M, int storage, int v);
 bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,
                       const float *vals, const float *g, float *out, float c2, float mu, int clip, cudaStream_t st,
                       cudaError_t *err);
 bool launch_box_shape_bf16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout,
                            const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out, float c2,
                            float mu, int clip, cudaStream_t st, cudaError_t *err);
+bool launch_box_shape_f16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const __half *wsrc,
+                          const __half *vals, const __half *g, __half *out, float c2, float mu, int clip,
+                          cudaStream_t st, cudaError_t *err);
 #define TNLM_BOX_DECL(V)                                                                                          \
     bool launch_box_var##V(int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,     \
                            const float *vals, const float *g, float *out, float c2, float mu, int clip,          \
                            cudaStream_t st, cudaError_t *err);                                                    \
     bool launch_box_var##V##_bf16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                \
                                   const uint16_t *wsrc, const uint16_t *vals, const uint16_t *g, uint16_t *out,   \
-                                  float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);
+                                  float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);              \
+    bool launch_box_var##V##_f16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                 \
+                                 const __half *wsrc, const __half *vals, const __half *g, __half *out, float c2,  \
+                                 float mu, int clip, cudaStream_t st, cudaError_t *err);
 TNLM_BOX_DECL(0)
 TNLM_BOX_DECL(1)
 TNLM_BOX_DECL(2)

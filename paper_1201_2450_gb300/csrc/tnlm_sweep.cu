@@ -180,18 +180,20 @@ size_t sweep_smem(int d, int M)
 }  // namespace
 
 // Launch shape of the box-sum sweep per (d, M, storage type); 0 until tnlm_autotune measures another.
-static int g_box_shape[4][5][2] = {};
+static int g_box_shape[4][5][3] = {};
 
-int box_shape(int d, int M, int bf16)
+static int storage_index(int storage) { return storage == 0 ? 0 : (storage == 2 ? 2 : 1); }
+
+int box_shape(int d, int M, int storage)
 {
     if (d < 0 || d > 3 || M < 0 || M > 4) return 0;
-    return g_box_shape[d][M][bf16 ? 1 : 0];
+    return g_box_shape[d][M][storage_index(storage)];
 }
 
-void set_box_shape(int d, int M, int bf16, int v)
+void set_box_shape(int d, int M, int storage, int v)
 {
     if (d < 0 || d > 3 || M < 0 || M > 4 || v < 0 || v >= kBoxShapes) return;
-    g_box_shape[d][M][bf16 ? 1 : 0] = v;
+    g_box_shape[d][M][storage_index(storage)] = v;
 }
 
 bool launch_box_shape(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const float *wsrc,
@@ -292,6 +294,39 @@ tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, cons
                          float *out, int d, int M, float h, float mu, int clip, cudaStream_t st)
 {
     return launch_sweep_range(nx, ny, nz, np, 0, np, wsrc, vals, g, out, d, M, h, mu, clip, st);
+}
+
+bool launch_box_shape_f16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const __half *wsrc,
+                          const __half *vals, const __half *g, __half *out, float c2, float mu, int clip,
+                          cudaStream_t st, cudaError_t *err)
+{
+    switch (v) {
+    case 1: return launch_box_var1_f16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 2: return launch_box_var2_f16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    case 3: return launch_box_var3_f16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    default: return launch_box_var0_f16(d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out, c2, mu, clip, st, err);
+    }
+}
+
+tnlm_status launch_sweep_range_f16(int nx, int ny, int nz, int np, int p0, int nout, const __half *wsrc,
+                                   const __half *vals, const __half *g, __half *out, int d, int M, float h, float mu,
+                                   int clip, cudaStream_t st)
+{
+    if (p0 < 0 || nout < 1 || p0 + nout > np) {
+        set_error("output phases [%d, %d) must lie in [0, %d)", p0, p0 + nout, np);
+        return TNLM_ERR_ARG;
+    }
+    cudaError_t err = cudaSuccess;
+    if (!launch_box_shape_f16(box_shape(d, M, 2), d, M, nx, ny, nz, np, p0, nout, wsrc, vals, g, out,
+                              exponent_scale(h), mu, clip, st, &err)) {
+        set_error("FP16 storage is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", d, M);
+        return TNLM_ERR_NOT_IMPLEMENTED;
+    }
+    if (err != cudaSuccess) {
+        set_error("FP16 sweep launch failed: %s", cudaGetErrorString(err));
+        return TNLM_ERR_CUDA;
+    }
+    return TNLM_OK;
 }
 
 tnlm_status launch_sweep_range_bf16(int nx, int ny, int nz, int np, int p0, int nout, const uint16_t *wsrc,
