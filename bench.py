@@ -167,11 +167,32 @@ def projection_nnz(desc: dict, device="cuda") -> int:
     """Non-zeros of P: the number of (ray, cell) pairs with a positive chord,
     i.e. cells crossed per ray = 1 + sum over axes of |exit cell - entry cell|
     (FP64, counted view by view on the device)."""
+    return projection_counts(desc, device)[0]
+
+
+# FP32 operations of the projector's slab walk, counted from its source (an FMA counts 2): per
+# dominant-axis slab 12 (slab end, crossing test and select, two segment lengths and FMAs, the next
+# plane by one FMA), per in-plane (b) crossing 3 more, per z (c) crossing 7 (its segment and the next
+# z plane); so per ray 12 (1 + |da|) + 3 |db| + 7 |dc| with da, db, dc the cell steps along each axis.
+K1_FLOP_SLAB, K1_FLOP_B, K1_FLOP_C = 12, 3, 7
+# FP32 operations of the band transpose per non-zero of P, counted from its source on this geometry:
+# per (column of 8 cells, view, pixel column) about 46 for the chord and row maps and 26 per cell
+# boundary (its row images, the band row split, the full-row prefix difference), 280 in all, plus
+# ~13 for the column's footprint per view shared by its ~3.5 pixel columns, over the ~38 (ray,
+# cell) pairs that chord serves (about 4.8 detector rows per 2 mm cell).
+K2_FLOP_PER_NNZ = 7.7
+
+
+def projection_counts(desc: dict, device="cuda") -> tuple[int, int]:
+    """(nnz(P), FP32 operations of the slab walk), exact per ray from the
+    entry and exit cells along each axis; the dominant axis is x or y (the
+    steeper of the two, z when steeper still), as in the kernel."""
     nu, nv = desc["nu"], desc["nv"]
     dev = torch.device(device)
     u = (torch.arange(nu, device=dev, dtype=torch.float64) - 0.5 * (nu - 1)) * desc["du"] + desc["u_off"]
     v = (torch.arange(nv, device=dev, dtype=torch.float64) - 0.5 * (nv - 1)) * desc["dv"] + desc["v_off"]
     V, U = torch.meshgrid(v, u, indexing="ij")
+    flops = 0
     n = [desc["nx"], desc["ny"], desc["nz"]]
     w = [desc["dx"], desc["dy"], desc["dz"]]
     b0 = [desc["cx"] - 0.5 * n[0] * w[0], desc["cy"] - 0.5 * n[1] * w[1], desc["cz"] - 0.5 * n[2] * w[2]]
@@ -191,20 +212,28 @@ def projection_nnz(desc: dict, device="cuda") -> int:
         hit = amin < amax
         eps = 1e-9
         cnt = torch.ones_like(U)
+        steps = []
         for k in range(3):
             ce = torch.floor((src[k] + (amin + eps) * d[k] - b0[k]) / w[k])
             cx_ = torch.floor((src[k] + (amax - eps) * d[k] - b0[k]) / w[k])
-            cnt += torch.abs(cx_ - ce)
-        total += int(torch.where(hit, cnt, torch.zeros_like(cnt)).sum().item())
-    return total
+            steps.append(torch.abs(cx_ - ce))
+            cnt += steps[-1]
+        g = [torch.abs(d[k]) / w[k] for k in range(3)]
+        zdom = (g[2] > g[0]) & (g[2] > g[1])
+        xa = ~zdom & (g[0] >= g[1])
+        sa = torch.where(zdom, steps[2], torch.where(xa, steps[0], steps[1]))
+        sb = torch.where(xa, steps[1], steps[0])
+        sc = torch.where(zdom, steps[1], steps[2])
+        fl = K1_FLOP_SLAB * (1 + sa) + K1_FLOP_B * sb + K1_FLOP_C * sc
+        zero = torch.zeros_like(cnt)
+        total += int(torch.where(hit, cnt, zero).sum().item())
+        flops += int(torch.where(hit, fl, zero).sum().item())
+    return total, flops
 
 
-# FP32 operations per algorithmic unit (the per-unit figures of the hot-path
-# analysis): projector 10 per non-zero of P (a ray-cell segment), transpose 15
-# per non-zero, sweep per pair evaluation 3*3*(2d+1) for the box-sum patch
-# distance plus 8 for the weight and the two accumulations (one exp besides).
-OPS_PER_NNZ_FORWARD = 10
-OPS_PER_NNZ_BACKPROJECT = 15
+# FP32 operations per pair evaluation of the sweep (the hot-path analysis's per-unit figure):
+# 3*3*(2d+1) for the box-sum patch distance plus 8 for the weight and the two accumulations
+# (one exp besides).
 
 
 def sweep_ops_per_pair(d: int) -> int:
@@ -343,8 +372,8 @@ def run_ours(args, rank, world, local):
     if t and t.get("source_sha") == _src_sha(KERNEL_SRC[dom]) and cfg.n_phases == 10:
         traffic = t["bytes_per_launch"]
     # the three kernels are bound by FP32 / integer issue, not HBM: roofline against the FP32 peak
-    nnz = projection_nnz(pb.geom)
-    work = {"k_forward": OPS_PER_NNZ_FORWARD * nnz, "k_backproject": OPS_PER_NNZ_BACKPROJECT * nnz,
+    nnz, k1_flop = projection_counts(pb.geom)
+    work = {"k_forward": k1_flop, "k_backproject": K2_FLOP_PER_NNZ * nnz,
             "k_sweep": sweep_ops_per_pair(cfg.d) * sweep_pairs(cfg)}
     peak_t = cpk["fp32_tflops"]
     alu = {n: {"algorithmic_tflop": round(work[n] / 1e12, 4),
