@@ -139,6 +139,21 @@ tnlm_status tnlm_gauss_jacobi(int nx, int ny, int nz, int n_phases, const float 
                               const float *g, float *f_out, int d, int M, float h, float mu, int clip,
                               void *stream);
 
+/* The sweep of tnlm_gauss_jacobi with the symmetric reuse of Sec. 2.4: the
+ * patch distance between x in phase i and x + delta in phase i+1 serves both
+ * the output x of phase i (toward i+1) and the output x + delta of phase i+1
+ * (toward i, offset -delta), so each phase pair's distances are computed
+ * once.  Per pair one pass computes phase i toward i+1 and writes every
+ * distance to a buffer; a second pass gives phase i+1 toward i from it (the
+ * exponentials and sums only).  Allocates two buffers of (2M+1)^3 nx ny nz
+ * floats stream-ordered per call (TNLM_ERR_OOM if that fails).  FP32
+ * storage, d in {1,2}, M in {1,2,3}; results agree with tnlm_gauss_jacobi
+ * to rounding (the distances are the same sums, up to the association of
+ * one of their partial sums). */
+tnlm_status tnlm_gauss_jacobi_pairs(int nx, int ny, int nz, int n_phases, const float *wsrc, const float *vals,
+                                    const float *g, float *f_out, int d, int M, float h, float mu, int clip,
+                                    void *stream);
+
 /* One Gauss-Jacobi sweep of Eq. 8, as tnlm_gauss_jacobi, for the output
  * phases p0 .. p0 + n_out - 1 only, of arrays ([n_phases][nz][ny][nx]) of
  * n_phases phases whose ring neighbours are (i +- 1) mod n_phases.  The

@@ -32,6 +32,7 @@ __all__ = [
     "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path", "tnlm_peak_probe", "tnlm_gauss_jacobi_range", "tnlm_p1",
     "tnlm_reconstruct_fp16", "tnlm_enhance_fp16", "tnlm_gauss_jacobi_fp16", "tnlm_energy_grad_fp16",
+    "tnlm_gauss_jacobi_pairs",
 ]
 
 _lock = threading.Lock()
@@ -111,6 +112,7 @@ def _load():
             "tnlm_weights": (i, [i, i, i, i, vp, i, i, f, vp, sz, vp]),
             "tnlm_gauss_jacobi": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_gauss_jacobi_range": (i, [i, i, i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_gauss_jacobi_pairs": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_p1": (i, [vp, vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
@@ -284,6 +286,20 @@ def tnlm_gauss_jacobi(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d
     _check(_load().tnlm_gauss_jacobi(nx, ny, nz, np_, _dev(wsrc, "wsrc"), _dev(vals, "vals", dev, wsrc.shape),
                                      _dev(g, "g", dev, wsrc.shape), _dev(out, "f_out", dev, wsrc.shape), d, M, h,
                                      mu, int(clip), _stream(stream)), "tnlm_gauss_jacobi")
+    return out
+
+
+def tnlm_gauss_jacobi_pairs(wsrc: torch.Tensor, vals: torch.Tensor, g: torch.Tensor, d: int, M: int, h: float,
+                            mu: float, clip: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One Eq. 8 sweep with each phase pair's patch distances computed once
+    (Sec. 2.4); the same result as tnlm_gauss_jacobi to rounding."""
+    np_, nz, ny, nx = wsrc.shape
+    if out is None:
+        out = torch.empty_like(wsrc)
+    dev = wsrc.device
+    _check(_load().tnlm_gauss_jacobi_pairs(nx, ny, nz, np_, _dev(wsrc, "wsrc"), _dev(vals, "vals", dev, wsrc.shape),
+                                           _dev(g, "g", dev, wsrc.shape), _dev(out, "f_out", dev, wsrc.shape), d, M,
+                                           h, mu, int(clip), _stream(stream)), "tnlm_gauss_jacobi_pairs")
     return out
 
 

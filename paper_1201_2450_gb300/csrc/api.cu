@@ -700,6 +700,32 @@ tnlm_status tnlm_reconstruct_batch(int n, tnlm_geometry *const *geoms, const flo
     return st;
 }
 
+tnlm_status tnlm_gauss_jacobi_pairs(int nx, int ny, int nz, int np, const float *wsrc, const float *vals,
+                                    const float *g, float *f_out, int d, int M, float h, float mu, int clip,
+                                    void *stream)
+{
+    TNLM_TRY(check_sweep_args(nx, ny, nz, np, d, M, h, mu));
+    if (!wsrc || !vals || !g || !f_out) return arg_error("wsrc, vals, g and f_out must not be NULL");
+    if (f_out == wsrc || f_out == vals || f_out == g) return arg_error("f_out must not alias wsrc, vals or g");
+    if (!((d == 1 || d == 2) && M >= 1 && M <= 3)) {
+        set_error("the phase-pair sweep is available for d in {1,2} and M in {1,2,3} (got d=%d, M=%d)", d, M);
+        return TNLM_ERR_NOT_IMPLEMENTED;
+    }
+    const size_t W = (size_t)(2 * M + 1) * (2 * M + 1) * (2 * M + 1);
+    const size_t n = W * (size_t)nx * ny * nz;
+    cudaStream_t st = as_stream(stream);
+    float *G = nullptr;
+    if (forced_alloc_failure() || cudaMallocAsync(reinterpret_cast<void **>(&G), sizeof(float) * 2 * n, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocAsync of the two distance buffers (%zu bytes) failed", sizeof(float) * 2 * n);
+        return TNLM_ERR_OOM;
+    }
+    tnlm_status status = TNLM_OK;
+    launch_sweep_pairs(d, M, nx, ny, nz, np, wsrc, vals, g, f_out, h, mu, clip, G, G + n, st, &status);
+    cudaFreeAsync(G, st);
+    return status;
+}
+
 tnlm_status tnlm_gauss_jacobi_range(int nx, int ny, int nz, int np, int p0, int n_out, const float *wsrc,
                                     const float *vals, const float *g, float *f_out, int d, int M, float h, float mu,
                                     int clip, void *stream)

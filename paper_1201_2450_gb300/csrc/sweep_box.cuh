@@ -124,10 +124,13 @@ __device__ __forceinline__ float2 xbox2(float2 b)
 // One direction of the sweep for this thread's 2 x BZ outputs (y rows j = 0, 1
 // are processed as FP32x2 pairs).  ai holds the thread's patch block of phase
 // i as [z][y pair]; res accumulates N/Z per output.
-template <int D_, int M_, int BZ, int WY_, int WZ_, bool INTERIOR>
+// STORE: also write every patch distance of the thread's outputs to Gd[delta][voxel] (delta-major, delta =
+// ((dz + M) S + dy + M) S + dx + M), for the phase-pair form of the sweep (k_pair_b reads them back).
+template <int D_, int M_, int BZ, int WY_, int WZ_, bool INTERIOR, bool STORE = false>
 __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2 + 2 * D_) / 2], const float *s_aj,
                                               const float *s_vj, int lane, int wy, int wz, int x, int yb, int zb,
-                                              int nx, int ny, int nz, float c2, float2 (&res)[BZ])
+                                              int nx, int ny, int nz, float c2, float2 (&res)[BZ],
+                                              float *__restrict__ Gd = nullptr, bool st0 = false, bool st1 = false)
 {
     constexpr int BY = 2;
     using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
@@ -203,6 +206,17 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
                     for (int yy = 2; yy <= 2 * D_; ++yy) m += (yy & 1) ? bz[k][yy / 2].y : bz[k][yy / 2].x;
                     const float2 yb2 = make_float2(bz[k][0].x + m, m + bz[k][SP - 1].y);
                     const float2 Dv = xbox2<D_>(yb2);  // patch distances of outputs (0,k) and (1,k)
+                    if constexpr (STORE) {
+                        constexpr int S = 2 * M_ + 1;
+                        const long long nvox = (long long)nx * ny * nz;
+                        const int z = zb + k;
+                        if (z < nz) {
+                            float *gp = Gd + (long long)((q * S + dy + M_) * S + dx + M_) * nvox +
+                                        ((long long)z * ny + yb) * nx + x;
+                            if (st0) gp[0] = Dv.x;
+                            if (st1) gp[nx] = Dv.y;
+                        }
+                    }
                     float2 a = __ffma2_rn(Dv, nc2, mref[k]);  // log2 weights vs the references
                     const bool vz = INTERIOR || (unsigned)(zb + k + q - M_) < (unsigned)nz;
                     if (!INTERIOR) {

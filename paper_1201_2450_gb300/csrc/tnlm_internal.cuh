@@ -102,6 +102,11 @@ tnlm_status launch_sweep_range_f16(int nx, int ny, int nz, int np, int p0, int n
                                    int clip, cudaStream_t st);
 tnlm_status launch_weights(int nx, int ny, int nz, int np, const float *wsrc, int d, int M, float h, float *w,
                            cudaStream_t st);
+// The sweep with the patch distances of each phase pair computed once (sweep_pairs.cu): G0, G1 hold
+// (2M+1)^3 nx ny nz floats each; false when (d, M) has no box kernel.
+bool launch_sweep_pairs(int d, int M, int nx, int ny, int nz, int np, const float *wsrc, const float *vals,
+                        const float *g, float *out, float h, float mu, int clip, float *G0, float *G1, cudaStream_t st,
+                        tnlm_status *status);
 // BF16 images (bit patterns), FP32 arithmetic; box configurations only
 tnlm_status launch_sweep_bf16(int nx, int ny, int nz, int np, const uint16_t *wsrc, const uint16_t *vals,
                               const uint16_t *g, uint16_t *out, int d, int M, float h, float mu, int clip, cudaStream_t st);
