@@ -611,6 +611,12 @@ def measure_batch(tnlm, synth, stream, n_outer: int = 20) -> dict:
 
     bat_ms = _time_ms(lambda: run_plan(plan, fs), stream, reps=1)
     plan.close()
+    fg = [torch.zeros_like(f) for f in fs]
+    gplan = tnlm.BatchPlan(geoms, ys, fg, params, grouped=True)
+    grp_ms = _time_ms(lambda: run_plan(gplan, fg), stream, reps=1)
+    gplan.close()
+    grouped_equal = all(bool(torch.equal(a, b)) for a, b in zip(fg, fs))
+    del fg
     ys16 = [y.bfloat16() for y in ys]
     fs16 = [torch.zeros(g.vol_shape, device="cuda", dtype=torch.bfloat16) for g in geoms]
     plan16 = tnlm.BatchPlan(geoms, ys16, fs16, params)
@@ -624,6 +630,8 @@ def measure_batch(tnlm, synth, stream, n_outer: int = 20) -> dict:
                                f"384x288 or 512x384), {n_outer} FBS iterations each, autotuned launch shapes",
            "batch16_total_voxels": voxels,
            "batch16_graph_ms": round(bat_ms, 2), "batch16_sequential_ms": round(seq_ms, 2),
+           "batch16_grouped_persistent_sweep_ms": round(grp_ms, 2),
+           "batch16_grouped_equals_graph_bitwise": grouped_equal,
            "batch16_graph_problem_iterations_per_s": round(n_it / (bat_ms / 1e3), 3),
            "batch16_sequential_problem_iterations_per_s": round(n_it / (seq_ms / 1e3), 3),
            "batch16_bf16_graph_ms": round(b16_ms, 2),

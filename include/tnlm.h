@@ -236,6 +236,17 @@ typedef struct tnlm_batch_plan tnlm_batch_plan;
 tnlm_status tnlm_batch_plan_create(int n_problems, tnlm_geometry *const *geoms, const float *const *y,
                                    float *const *f, const tnlm_params *params, tnlm_batch_plan **out);
 tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *stream);
+/* How a plan made afterwards runs the Eq. 8 sweeps (process-wide; plans keep
+ * the form they were made with): 0 (default) each problem's sweep on its own
+ * branch of the graph; 1 one persistent launch for the sweeps of all problems
+ * -- resident CTAs take (problem, tile) items from a device counter until
+ * none is left, each tile computed as in the per-problem sweep (same results)
+ * -- after every problem's (P1).  Mode 1 applies to FP32 plans whose problems
+ * share (d, M) with d in {1,2}, M in {1,2,3}, n_gj = 1 and gj_start = 0; other
+ * plans use mode 0.  A mode-1 plan holds a small device array of problem
+ * descriptors; destroying it waits for the device to finish its replays. */
+tnlm_status tnlm_set_batch_sweep_mode(int mode);
+
 /* The same plan for problems stored in BF16 (as tnlm_reconstruct_bf16). */
 tnlm_status tnlm_batch_plan_create_bf16(int n_problems, tnlm_geometry *const *geoms, const uint16_t *const *y,
                                         uint16_t *const *f, const tnlm_params *params, tnlm_batch_plan **out);

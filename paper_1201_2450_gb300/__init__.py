@@ -113,6 +113,7 @@ def _load():
             "tnlm_gauss_jacobi": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_gauss_jacobi_range": (i, [i, i, i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
             "tnlm_gauss_jacobi_pairs": (i, [i, i, i, i, vp, vp, vp, vp, i, i, f, f, i, vp]),
+            "tnlm_set_batch_sweep_mode": (i, [i]),
             "tnlm_p1": (i, [vp, vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
@@ -420,14 +421,20 @@ class BatchPlan:
     run(k) replays it k times, updating every f in place.  The plan keeps
     references to the geometries and tensors it was built on."""
 
-    def __init__(self, geoms, ys, fs, params):
+    def __init__(self, geoms, ys, fs, params, grouped: bool = False):
+        """grouped: the sweeps of all problems in one persistent launch
+        (tnlm_set_batch_sweep_mode(1) while the plan is made)."""
         dtype = fs[0].dtype if len(fs) > 0 else torch.float32
         n, G, Y, F, P = _batch_args(geoms, ys, fs, params, dtype)
         self._keep = (list(geoms), list(ys), list(fs))
         self.handle = C.c_void_p()
         create = {torch.bfloat16: _load().tnlm_batch_plan_create_bf16,
                   torch.float16: _load().tnlm_batch_plan_create_fp16}.get(dtype, _load().tnlm_batch_plan_create)
-        _check(create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
+        _check(_load().tnlm_set_batch_sweep_mode(1 if grouped else 0), "tnlm_set_batch_sweep_mode")
+        try:
+            _check(create(n, G, Y, F, P, C.byref(self.handle)), "tnlm_batch_plan_create")
+        finally:
+            _load().tnlm_set_batch_sweep_mode(0)
 
     def run(self, n_iterations: int, stream=None):
         _check(_load().tnlm_batch_plan_run(self.handle, int(n_iterations), _stream(stream)), "tnlm_batch_plan_run")

@@ -550,22 +550,88 @@ tnlm_status tnlm_reconstruct_fp16(tnlm_geometry *geo, const uint16_t *y, uint16_
 struct tnlm_batch_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    void *group_mem = nullptr;  // grouped sweep: problem descriptors and the work counter
 };
+
+static int g_batch_sweep_mode = 0;  // 0: each problem's sweep on its branch; 1: one grouped persistent sweep
+
+tnlm_status tnlm_set_batch_sweep_mode(int mode)
+{
+    if (mode != 0 && mode != 1) return arg_error("batch sweep mode must be 0 (per problem) or 1 (grouped)");
+    g_batch_sweep_mode = mode;
+    return TNLM_OK;
+}
 
 }  // extern "C"
 
 // Validate and prepare every problem, then capture one FBS iteration of all of
 // them into *graph: the capture stream forks to up to 8 side streams (problem
 // b on side stream b mod 8) and joins back.
+// The grouped sweep applies to FP32 problems that share (d, M) of a box kernel and sweep once from g^(k).
+template <class T>
+static bool grouped_applies(int n, const tnlm_params *params)
+{
+    if (!std::is_same<T, float>::value || g_batch_sweep_mode != 1) return false;
+    for (int b = 0; b < n; ++b) {
+        const tnlm_params &p = params[b];
+        if (p.n_gj > 1 || p.gj_start != 0 || p.d != params[0].d || p.M != params[0].M) return false;
+    }
+    const int d = params[0].d, M = params[0].M;
+    return (d == 1 || d == 2) && M >= 1 && M <= 3;
+}
+
+// Descriptors of a grouped sweep in device memory (and its counter), filled before the capture.
+static tnlm_status prepare_grouped(int n, tnlm_geometry *const *geoms, float *const *f, const tnlm_params *params,
+                                   void **mem, long long *total)
+{
+    const int d = params[0].d, M = params[0].M, v = box_shape(d, M, 0);
+    std::vector<GroupSweep> h((size_t)n);
+    long long first = 0;
+    for (int b = 0; b < n; ++b) {
+        const KGeom &kg = geoms[b]->kg;
+        GroupSweep &q = h[(size_t)b];
+        long long items = 0;
+        box_grouped_tiles(v, d, M, kg.nx, kg.ny, kg.nz, kg.np, &q.ntx, &q.nty, &q.ntz, &items);
+        q.wsrc = q.vals = q.g = geoms[b]->d_g;
+        q.out = f[b];
+        q.nx = kg.nx;
+        q.ny = kg.ny;
+        q.nz = kg.nz;
+        q.np = kg.np;
+        q.first = first;
+        q.c2 = (float)(1.4426950408889634 / (2.0 * (double)params[b].h * (double)params[b].h));
+        q.mu = params[b].mu;
+        q.clip = params[b].clip_nonneg;
+        first += items;
+    }
+    *total = first;
+    const size_t bytes = sizeof(GroupSweep) * (size_t)n + sizeof(unsigned long long);
+    if (forced_alloc_failure() || cudaMalloc(mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *mem = nullptr;
+        set_error("cudaMalloc of the grouped sweep's descriptors failed");
+        return TNLM_ERR_OOM;
+    }
+    TNLM_TRY_CUDA(cudaMemcpy(*mem, h.data(), sizeof(GroupSweep) * (size_t)n, cudaMemcpyHostToDevice));
+    return TNLM_OK;
+}
+
 template <class T>
 static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const T *const *y, T *const *f,
-                                 const tnlm_params *params, cudaGraph_t *graph)
+                                 const tnlm_params *params, cudaGraph_t *graph, void **group_mem)
 {
     if (n < 1 || !geoms || !y || !f || !params) return arg_error("need n >= 1 and non-NULL arrays");
     for (int b = 0; b < n; ++b) {
         for (int c = 0; c < b; ++c)
             if (geoms[c] == geoms[b]) return arg_error("a geometry handle may appear once per batch (it owns the workspace)");
         TNLM_TRY(prepare_reconstruct(geoms[b], y[b], f[b], &params[b], 1, !std::is_same<T, float>::value));
+    }
+    const bool grouped = grouped_applies<T>(n, params);
+    long long total = 0;
+    int sms = 0;
+    if (grouped) {
+        TNLM_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geoms[0]->device));
+        TNLM_TRY(prepare_grouped(n, geoms, reinterpret_cast<float *const *>(f), params, group_mem, &total));
     }
     const int ns = n < 8 ? n : 8;  // parallel branches of the graph
     cudaStream_t cs = nullptr;
@@ -591,12 +657,25 @@ static tnlm_status capture_batch(int n, tnlm_geometry *const *geoms, const T *co
         cuda_ok(cudaEventRecord(fork, cs), "cudaEventRecord");
         for (int s = 0; s < ns; ++s) cuda_ok(cudaStreamWaitEvent(side[s], fork, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < n && status == TNLM_OK; ++b) {
-            tnlm_status sb = fbs_iteration<T>(geoms[b], y[b], f[b], &params[b], 0, false, nullptr, side[b % ns]);
+            tnlm_status sb = grouped ? p1_step<T>(geoms[b], y[b], f[b], reinterpret_cast<T *>(geoms[b]->d_g), &params[b],
+                                                  0, false, nullptr, side[b % ns])
+                                     : fbs_iteration<T>(geoms[b], y[b], f[b], &params[b], 0, false, nullptr,
+                                                        side[b % ns]);
             if (sb != TNLM_OK) status = sb;
         }
         for (int s = 0; s < ns; ++s) {
             cudaEventRecord(join[s], side[s]);
             cudaStreamWaitEvent(cs, join[s], 0);
+        }
+        if (grouped && status == TNLM_OK) {
+            // every problem's sweep in one persistent launch, after every problem's (P1)
+            auto *probs = static_cast<const GroupSweep *>(*group_mem);
+            auto *counter = reinterpret_cast<unsigned long long *>(static_cast<GroupSweep *>(*group_mem) + n);
+            cuda_ok(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), cs), "cudaMemsetAsync");
+            cudaError_t err = cudaSuccess;
+            launch_box_grouped(box_shape(params[0].d, params[0].M, 0), params[0].d, params[0].M, probs, n, total,
+                               counter, sms, cs, &err);
+            cuda_ok(err, "grouped sweep launch");
         }
         cudaGraph_t gr = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &gr);  // always ends the capture, also after an error
@@ -621,11 +700,17 @@ static tnlm_status plan_create(int n, tnlm_geometry *const *geoms, const T *cons
     if (!out) return arg_error("out must not be NULL");
     *out = nullptr;
     cudaGraph_t graph = nullptr;
-    TNLM_TRY(capture_batch<T>(n, geoms, y, f, params, &graph));
+    void *group_mem = nullptr;
+    const tnlm_status cs = capture_batch<T>(n, geoms, y, f, params, &graph, &group_mem);
+    if (cs != TNLM_OK) {
+        cudaFree(group_mem);
+        return cs;
+    }
     cudaGraphExec_t exec = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
+        cudaFree(group_mem);
         set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
         return TNLM_ERR_CUDA;
     }
@@ -633,11 +718,13 @@ static tnlm_status plan_create(int n, tnlm_geometry *const *geoms, const T *cons
     if (!plan) {
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
+        cudaFree(group_mem);
         set_error("out of host memory");
         return TNLM_ERR_OOM;
     }
     plan->graph = graph;
     plan->exec = exec;
+    plan->group_mem = group_mem;
     *out = plan;
     return TNLM_OK;
 }
@@ -676,9 +763,12 @@ tnlm_status tnlm_batch_plan_run(tnlm_batch_plan *plan, int n_iterations, void *s
 void tnlm_batch_plan_destroy(tnlm_batch_plan *plan)
 {
     if (!plan) return;
-    // an executable graph still in flight is freed by the driver when its launches complete
+    // an executable graph still in flight is freed by the driver when its launches complete; the
+    // grouped sweep's descriptors are read by those launches, so they are freed after the device drains
+    if (plan->group_mem) cudaDeviceSynchronize();
     cudaGraphExecDestroy(plan->exec);
     cudaGraphDestroy(plan->graph);
+    cudaFree(plan->group_mem);
     delete plan;
 }
 

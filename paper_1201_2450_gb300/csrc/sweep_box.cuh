@@ -253,25 +253,19 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
     }
 }
 
+// One tile (tx_i, ty_i, tz_i) of output phase i (ring neighbours (i +- 1) mod np) of the box-sum
+// sweep, by the whole CTA; sm: the CTA's dynamic shared memory.
 template <int D_, int M_, int BY, int BZ, int WY_, int WZ_, class T>
-__global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
-    k_sweep_box(int nx, int ny, int nz, int np, int p0, int ntx, int nty, int ntz, const T *__restrict__ wsrc,
-                const T *__restrict__ vals, const T *__restrict__ g, T *__restrict__ out, float c2,
-                float mu, int clip)
+__device__ __forceinline__ void sweep_box_tile(int nx, int ny, int nz, int np, int tx_i, int ty_i, int tz_i, int i,
+                                               const T *__restrict__ wsrc, const T *__restrict__ vals,
+                                               const T *__restrict__ g, T *__restrict__ out, float c2, float mu,
+                                               int clip, float *sm)
 {
     using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
-    extern __shared__ float sm[];
     float *s_aj = sm;
     float *s_vj = sm + C::AJX * C::AJY * C::AJZ;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wy = warp % C::WY, wz = warp / C::WY;
-    int b = blockIdx.x;
-    const int tx_i = b % ntx;
-    b /= ntx;
-    const int ty_i = b % nty;
-    b /= nty;
-    const int tz_i = b % ntz;
-    const int i = p0 + b / ntz;  // output phase (ring neighbours (i +- 1) mod np)
     const int X0 = tx_i * C::TXO, Y0 = ty_i * C::TY, Z0 = tz_i * C::TZ;
     const int x = X0 - D_ + lane;
     const int yb = Y0 + wy * BY, zb = Z0 + wz * BZ;
@@ -328,6 +322,86 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
     }
 }
 
+template <int D_, int M_, int BY, int BZ, int WY_, int WZ_, class T>
+__global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
+    k_sweep_box(int nx, int ny, int nz, int np, int p0, int ntx, int nty, int ntz, const T *__restrict__ wsrc,
+                const T *__restrict__ vals, const T *__restrict__ g, T *__restrict__ out, float c2,
+                float mu, int clip)
+{
+    extern __shared__ float sm[];
+    int b = blockIdx.x;
+    const int tx_i = b % ntx;
+    b /= ntx;
+    const int ty_i = b % nty;
+    b /= nty;
+    const int tz_i = b % ntz;
+    sweep_box_tile<D_, M_, BY, BZ, WY_, WZ_, T>(nx, ny, nz, np, tx_i, ty_i, tz_i, p0 + b / ntz, wsrc, vals, g, out, c2,
+                                                mu, clip, sm);
+}
+
+// The sweeps of several problems with one (d, M) in one persistent launch: every CTA takes the next
+// (problem, tile) item from a device counter until none is left, and runs the tile as k_sweep_box
+// would (same operations in the same order, so the same results).  Items run problem by problem,
+// phase by phase, tile by tile.
+template <int D_, int M_, int BY, int BZ, int WY_, int WZ_>
+__global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
+    k_sweep_box_grouped(const GroupSweep *__restrict__ probs, int nprob, long long total,
+                        unsigned long long *__restrict__ counter)
+{
+    extern __shared__ float sm[];
+    __shared__ long long s_item;
+    for (;;) {
+        __syncthreads();  // the previous item is done with the shared memory and s_item
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= total) return;
+        int b = 0;
+        while (b + 1 < nprob && probs[b + 1].first <= it) ++b;
+        const GroupSweep P = probs[b];
+        long long r = it - P.first;
+        const int tx_i = (int)(r % P.ntx);
+        r /= P.ntx;
+        const int ty_i = (int)(r % P.nty);
+        r /= P.nty;
+        const int tz_i = (int)(r % P.ntz);
+        const int i = (int)(r / P.ntz);
+        sweep_box_tile<D_, M_, BY, BZ, WY_, WZ_, float>(P.nx, P.ny, P.nz, P.np, tx_i, ty_i, tz_i, i, P.wsrc, P.vals,
+                                                        P.g, P.out, P.c2, P.mu, P.clip, sm);
+    }
+}
+
+// the tiles of one problem of a grouped sweep, and the resident CTAs of the grouped kernel per SM
+template <int D_, int M_, int BZ, int WY_, int WZ_>
+bool grouped_tiles(int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz, long long *items)
+{
+    using C = BoxCfg<D_, M_, 2, BZ, WY_, WZ_>;
+    *ntx = (nx + C::TXO - 1) / C::TXO;
+    *nty = (ny + C::TY - 1) / C::TY;
+    *ntz = (nz + C::TZ - 1) / C::TZ;
+    *items = (long long)*ntx * *nty * *ntz * np;
+    return true;
+}
+
+template <int D_, int M_, int BZ, int WY_, int WZ_>
+bool launch_grouped(const GroupSweep *probs, int nprob, long long total, unsigned long long *counter, int sms,
+                    cudaStream_t st, cudaError_t *err)
+{
+    constexpr int BY = 2;
+    using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
+    auto kern = k_sweep_box_grouped<D_, M_, BY, BZ, WY_, WZ_>;
+    *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (*err != cudaSuccess) return true;
+    int per_sm = 0;
+    *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM);
+    if (*err != cudaSuccess) return true;
+    const long long ctas = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    kern<<<(unsigned)(ctas < total ? ctas : total), C::NT, C::SMEM, st>>>(probs, nprob, total, counter);
+    *err = cudaGetLastError();
+    return true;
+}
+
+
 // phases p0 .. p0 + nout - 1 of arrays of np phases
 template <int D_, int M_, int BZ, int WY_, int WZ_, class T>
 bool launch_box(int nx, int ny, int nz, int np, int p0, int nout, const T *wsrc, const T *vals, const T *g, T *out,
@@ -374,6 +448,40 @@ bool launch_shape(int d, int M, int nx, int ny, int nz, int np, int p0, int nout
     return false;
 }
 
+// (d, M) dispatch of the grouped sweep for launch shape V; false when (d, M) has no box kernel
+template <int V>
+bool grouped_shape(int d, int M, const GroupSweep *probs, int nprob, long long total, unsigned long long *counter,
+                   int sms, cudaStream_t st, cudaError_t *err)
+{
+    using S = BoxShape<V>;
+#define TNLM_GROUP_CASE(DD, MM)                                                                                   \
+    if (d == DD && M == MM) return launch_grouped<DD, MM, S::BZ, S::WY, S::WZ>(probs, nprob, total, counter, sms, st, err);
+    TNLM_GROUP_CASE(1, 1)
+    TNLM_GROUP_CASE(1, 2)
+    TNLM_GROUP_CASE(1, 3)
+    TNLM_GROUP_CASE(2, 1)
+    TNLM_GROUP_CASE(2, 2)
+    TNLM_GROUP_CASE(2, 3)
+#undef TNLM_GROUP_CASE
+    return false;
+}
+
+template <int V>
+bool grouped_tiles_shape(int d, int M, int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz, long long *items)
+{
+    using S = BoxShape<V>;
+#define TNLM_GTILE_CASE(DD, MM)                                                                                   \
+    if (d == DD && M == MM) return grouped_tiles<DD, MM, S::BZ, S::WY, S::WZ>(nx, ny, nz, np, ntx, nty, ntz, items);
+    TNLM_GTILE_CASE(1, 1)
+    TNLM_GTILE_CASE(1, 2)
+    TNLM_GTILE_CASE(1, 3)
+    TNLM_GTILE_CASE(2, 1)
+    TNLM_GTILE_CASE(2, 2)
+    TNLM_GTILE_CASE(2, 3)
+#undef TNLM_GTILE_CASE
+    return false;
+}
+
 }  // namespace box
 }  // namespace tnlm
 
@@ -395,6 +503,16 @@ bool launch_shape(int d, int M, int nx, int ny, int nz, int np, int p0, int nout
         return box::launch_shape<V, B>(d, M, nx, ny, nz, np, p0, nout, reinterpret_cast<const B *>(wsrc),       \
                                        reinterpret_cast<const B *>(vals), reinterpret_cast<const B *>(g),         \
                                        reinterpret_cast<B *>(out), c2, mu, clip, st, err);                        \
+    }                                                                                                             \
+    bool launch_box_grouped_var##V(int d, int M, const GroupSweep *probs, int nprob, long long total,            \
+                                   unsigned long long *counter, int sms, cudaStream_t st, cudaError_t *err)       \
+    {                                                                                                             \
+        return box::grouped_shape<V>(d, M, probs, nprob, total, counter, sms, st, err);                           \
+    }                                                                                                             \
+    bool box_grouped_tiles_var##V(int d, int M, int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz,     \
+                                  long long *items)                                                               \
+    {                                                                                                             \
+        return box::grouped_tiles_shape<V>(d, M, nx, ny, nz, np, ntx, nty, ntz, items);                           \
     }                                                                                                             \
     bool launch_box_var##V##_f16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                 \
                                  const __half *wsrc, const __half *vals, const __half *g, __half *out, float c2,  \

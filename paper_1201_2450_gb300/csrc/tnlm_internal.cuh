@@ -177,6 +177,22 @@ int cgls_partial_len(int np);
 
 tnlm_status check_sweep_args(int nx, int ny, int nz, int np, int d, int M, float h, float mu);
 
+// One problem of a grouped (persistent, multi-problem) sweep: its arrays, sizes, tile grid and the
+// index of its first work item.
+struct GroupSweep {
+    const float *wsrc, *vals, *g;
+    float *out;
+    int nx, ny, nz, np;
+    int ntx, nty, ntz;
+    long long first;
+    float c2, mu;
+    int clip;
+};
+bool launch_box_grouped(int v, int d, int M, const GroupSweep *probs, int nprob, long long total,
+                        unsigned long long *counter, int sms, cudaStream_t st, cudaError_t *err);
+bool box_grouped_tiles(int v, int d, int M, int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz,
+                       long long *items);
+
 // Box-sum sweep launch shapes (sweep_box.cuh); each returns false when (d, M)
 // has no box kernel.  box_shape / set_box_shape hold the process-wide choice
 // per (d, M, storage) that tnlm_autotune makes.
@@ -202,7 +218,11 @@ bool launch_box_shape_f16(int v, int d, int M, int nx, int ny, int nz, int np, i
                                   float c2, float mu, int clip, cudaStream_t st, cudaError_t *err);              \
     bool launch_box_var##V##_f16(int d, int M, int nx, int ny, int nz, int np, int p0, int nout,                 \
                                  const __half *wsrc, const __half *vals, const __half *g, __half *out, float c2,  \
-                                 float mu, int clip, cudaStream_t st, cudaError_t *err);
+                                 float mu, int clip, cudaStream_t st, cudaError_t *err);                          \
+    bool launch_box_grouped_var##V(int d, int M, const GroupSweep *probs, int nprob, long long total,            \
+                                   unsigned long long *counter, int sms, cudaStream_t st, cudaError_t *err);      \
+    bool box_grouped_tiles_var##V(int d, int M, int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz,     \
+                                  long long *items);
 TNLM_BOX_DECL(0)
 TNLM_BOX_DECL(1)
 TNLM_BOX_DECL(2)

@@ -296,6 +296,28 @@ tnlm_status launch_sweep(int nx, int ny, int nz, int np, const float *wsrc, cons
     return launch_sweep_range(nx, ny, nz, np, 0, np, wsrc, vals, g, out, d, M, h, mu, clip, st);
 }
 
+bool launch_box_grouped(int v, int d, int M, const GroupSweep *probs, int nprob, long long total,
+                        unsigned long long *counter, int sms, cudaStream_t st, cudaError_t *err)
+{
+    switch (v) {
+    case 1: return launch_box_grouped_var1(d, M, probs, nprob, total, counter, sms, st, err);
+    case 2: return launch_box_grouped_var2(d, M, probs, nprob, total, counter, sms, st, err);
+    case 3: return launch_box_grouped_var3(d, M, probs, nprob, total, counter, sms, st, err);
+    default: return launch_box_grouped_var0(d, M, probs, nprob, total, counter, sms, st, err);
+    }
+}
+
+bool box_grouped_tiles(int v, int d, int M, int nx, int ny, int nz, int np, int *ntx, int *nty, int *ntz,
+                       long long *items)
+{
+    switch (v) {
+    case 1: return box_grouped_tiles_var1(d, M, nx, ny, nz, np, ntx, nty, ntz, items);
+    case 2: return box_grouped_tiles_var2(d, M, nx, ny, nz, np, ntx, nty, ntz, items);
+    case 3: return box_grouped_tiles_var3(d, M, nx, ny, nz, np, ntx, nty, ntz, items);
+    default: return box_grouped_tiles_var0(d, M, nx, ny, nz, np, ntx, nty, ntz, items);
+    }
+}
+
 bool launch_box_shape_f16(int v, int d, int M, int nx, int ny, int nz, int np, int p0, int nout, const __half *wsrc,
                           const __half *vals, const __half *g, __half *out, float c2, float mu, int clip,
                           cudaStream_t st, cudaError_t *err)

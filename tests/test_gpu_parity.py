@@ -1037,3 +1037,38 @@ def test_reconstruct_resumes_from_its_iterate():
     torch.cuda.synchronize()
     assert torch.equal(f, f5)
     G.close()
+
+
+def test_grouped_persistent_sweep_equals_per_problem_plan(ora):
+    """Uneven problems sharing (d, M) = (1, 3): the plan whose sweeps run as one
+    persistent launch (CTAs taking (problem, tile) items from a device
+    counter) gives the per-problem plan's images bit for bit, and the oracle's
+    TNLM-R to 1e-5."""
+    cfgs = [synth.ReconConfig("grouped batch problem", nph, vol, 512.0 / vol[0], views, det, 399.4 / det[0], 5e4,
+                              1, 3, 0.02, 1.0, 3, "thorax", 2200 + k)
+            for k, (nph, vol, views, det) in enumerate([(3, (32, 32, 12), [5, 6, 4], (48, 36)),
+                                                        (4, (40, 40, 16), [4, 5, 6, 5], (64, 48)),
+                                                        (2, (24, 24, 9), [6, 5], (40, 30))])]
+    probs = [synth.recon_problem(c) for c in cfgs]
+    params = []
+    for k, pb in enumerate(probs):
+        OG = ora.Geometry(pb.geom)
+        tau = float(np.float32(1.0 / ora.power_norm(OG, synth.uniform(OG.vol_shape, 800 + k), 30)))
+        params.append(tnlm.Params(d=1, M=3, h=0.02, mu=1.0, tau=tau, n_outer=3))
+    Gs = [tnlm.Geometry(pb.geom) for pb in probs]
+    ys = [cuda(pb.y.numpy()) for pb in probs]
+    f_plain = [torch.zeros(G.vol_shape, device="cuda") for G in Gs]
+    f_group = [torch.zeros(G.vol_shape, device="cuda") for G in Gs]
+    p1 = tnlm.BatchPlan(Gs, ys, f_plain, params)
+    p1.run(3)
+    p1.close()
+    p2 = tnlm.BatchPlan(Gs, ys, f_group, params, grouped=True)
+    p2.run(2)
+    p2.run(1)
+    p2.close()
+    torch.cuda.synchronize()
+    for a, b in zip(f_plain, f_group):
+        assert torch.equal(a, b)
+    pb, p = probs[1], params[1]
+    ref = ora.reconstruct(ora.Geometry(pb.geom), pb.y.numpy(), np.zeros(Gs[1].vol_shape), p.tau, 1, 3, 0.02, 1.0, 3)
+    assert rel_l2(f_group[1].cpu().numpy(), ref) <= RTOL
