@@ -47,12 +47,11 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # measured on; a changed source invalidates the figure (reported as null).
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
-    # the transpose stage is the column scan plus the band kernel
-    "k_forward": {"bytes_per_launch": int((272.985856e6 + 147.891456e6) * 10 / 6), "source_sha": "b3bfed95f4be8ebc"},
-    # (the scan and band kernels are unchanged since their capture; only k_forward changed in this file)
-    "k_backproject": {"bytes_per_launch": int((169.895936e6 + 284.310784e6 + 554.819840e6 + 92.989184e6) * 10 / 6),
-                      "source_sha": "b3bfed95f4be8ebc"},
-    "k_sweep": {"bytes_per_launch": int((159.0528e6 + 83.814912e6) * 10 / 6), "source_sha": "19521b83f7940da1"},
+    # the transpose stage is the column scan (its own earlier capture, source unchanged) plus the band kernel
+    "k_forward": {"bytes_per_launch": int((273.283328e6 + 147.755776e6) * 10 / 6), "source_sha": "a988298ded5a6752"},
+    "k_backproject": {"bytes_per_launch": int((169.895936e6 + 284.310784e6 + 557.578752e6 + 93.134080e6) * 10 / 6),
+                      "source_sha": "a988298ded5a6752"},
+    "k_sweep": {"bytes_per_launch": int((160.676608e6 + 84.272896e6) * 10 / 6), "source_sha": "5c1e717465e6a4bc"},
 }
 
 
@@ -307,13 +306,17 @@ def run_ours(args, rank, world, local):
     L = tnlm.tnlm_operator_norm(geom, x0, args.power_iters)
     tau = 1.0 / L
     params = tnlm.Params(d=cfg.d, M=cfg.M, h=cfg.h, mu=cfg.mu, tau=tau, n_outer=1, n_inner=1, clip_nonneg=1)
-    f = torch.zeros(geom.vol_shape, device="cuda")
+    # storage of y, f and the iteration's images: FP32 (the benchmark), or BF16 / FP16 with FP32 arithmetic
+    sdtype, recon = {"fp32": (torch.float32, tnlm.tnlm_reconstruct), "bf16": (torch.bfloat16, tnlm.tnlm_reconstruct_bf16),
+                     "fp16": (torch.float16, tnlm.tnlm_reconstruct_fp16)}[args.storage]
+    ys = y.to(sdtype).contiguous()
+    f = torch.zeros(geom.vol_shape, device="cuda", dtype=sdtype)
     stream = torch.cuda.current_stream()
     # launch shapes: timed once on this problem before the run (results do not depend on them)
     shapes = None if args.no_autotune else tnlm.tnlm_autotune(geom, params)
 
     for _ in range(args.warmup):
-        tnlm.tnlm_reconstruct(geom, y, f, params)
+        recon(geom, ys, f, params)
     torch.cuda.synchronize()
 
     geom.set_stage_timing(True)
@@ -325,7 +328,7 @@ def run_ours(args, rank, world, local):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        tnlm.tnlm_reconstruct(geom, y, f, params)
+        recon(geom, ys, f, params)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -340,7 +343,7 @@ def run_ours(args, rank, world, local):
     y_host = y.cpu().pin_memory()
     f_host = torch.zeros(geom.vol_shape).pin_memory()
     y_dev = torch.empty_like(y)
-    f_dev = torch.empty_like(f)
+    f_dev = torch.empty(geom.vol_shape, device="cuda")
     tnlm.reconstruct_host(geom, y_host, f_host, params, y_dev, f_dev)  # warm
     torch.cuda.synchronize()
     barrier(world)
@@ -416,6 +419,9 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": int(d2h)},
         "variants": variants,
     }
+    if args.storage != "fp32":
+        line["config"]["storage"] = f"{args.storage} storage of y, f and the iteration images, FP32 arithmetic"
+        line["config"]["workload"] += f" [{args.storage} storage]"
     if args.phases != 10:
         line["config"]["workload"] += f" [reduced to {args.phases} phases]"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -717,6 +723,8 @@ def main():
     ap.add_argument("--power-iters", type=int, default=20, help="power iterations that size the step tau")
     ap.add_argument("--no-variants", action="store_true", help="skip the FDK / CGLS / TNLM-E measurements")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32",
+                    help="storage of the images and projections in the timed loop (arithmetic stays FP32)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
