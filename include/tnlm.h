@@ -369,6 +369,17 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * tnlm_autotune_sweep does the same for the sweep alone (bf16 = 1: the BF16
  * storage kernels, 2: the FP16 ones; the argument of tnlm_set_sweep_shape
  * likewise), writing the chosen shape to *shape (nullable).
+ * The projector shape is 2, 4 or 8 (the slab walker: blocks of 32 x that
+ * many detector pixels, one ray per thread, each ray finding all its own
+ * crossings) or 102, 104 or 108 (the table walker: blocks of 32 x 2, 4 or 8
+ * pixels; the xy cells every detector column crosses are laid out once per
+ * handle in device memory, views x (nx + ny + 2) x nu entries of 8 bytes,
+ * and each ray adds only its own z crossings).  A new handle starts at 104;
+ * its tables are built, synchronising the device, by the first call that
+ * projects (or by tnlm_set_launch_shapes), never during a stream capture; if
+ * they cannot be allocated the slab walker with 4 rows runs.  The two
+ * walkers compute the same exact model but do not round alike, so the
+ * autotuner chooses within the walker that runs.
  * tnlm_set_launch_shapes / tnlm_set_sweep_shape set a shape directly
  * (TNLM_ERR_ARG for a shape that is not compiled).  The sweep-shape table
  * is shared by the whole process: change it from one host thread at a time

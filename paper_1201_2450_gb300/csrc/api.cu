@@ -62,8 +62,30 @@ static tnlm_status dev_alloc(T **p, size_t count)
     return TNLM_OK;
 }
 
+void ensure_coltab(tnlm_geometry *g)
+{
+    if (g->d_coltab || g->coltab_failed || g->kg.fwd_by < 100) return;
+    const size_t n = coltab_entries(g->kg, g->n_views_total);
+    if (forced_alloc_failure() || cudaMalloc(reinterpret_cast<void **>(&g->d_coltab), sizeof(float2) * n) != cudaSuccess) {
+        cudaGetLastError();
+        g->d_coltab = nullptr;
+        g->coltab_failed = true;
+        return;
+    }
+    if (build_coltab(g->kg, g->d_views, g->n_views_total, g->d_coltab, cudaStreamLegacy) != TNLM_OK ||
+        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(g->d_coltab);
+        g->d_coltab = nullptr;
+        g->coltab_failed = true;
+        return;
+    }
+    g->kg.coltab = g->d_coltab;
+}
+
 tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars)
 {
+    ensure_coltab(g);
     const KGeom &kg = g->kg;
     TNLM_TRY(dev_alloc(&g->d_r, (size_t)g->n_views_total * kg.npix));
     TNLM_TRY(dev_alloc(&g->d_g, (size_t)kg.np * kg.nvox));
@@ -277,9 +299,11 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry *
     k.alpha0 = (float)(d.sad / d.sdd);
     k.nvox = (long long)d.nx * d.ny * d.nz;
     k.npix = (long long)d.nu * d.nv;
-    k.fwd_by = 4;
     k.bp_by = 4;
     k.bp_ch = 8;
+    k.fwd_by = 104;  // the table projector once its tables are built (the slab walker until then)
+    k.coltab = nullptr;
+    k.coltab_kmax = coltab_kmax(k);
     g->n_views_total = (int)total;
     g->n_views.assign(d.n_views, d.n_views + d.n_phases);
     g->angles.assign(d.angles_rad, d.angles_rad + total);
@@ -322,6 +346,7 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_part);
     cudaFree(g->d_scalars);
     cudaFree(g->d_pref);
+    cudaFree(g->d_coltab);
     cudaFree(g->d_q);
     cudaFree(g->d_s);
     cudaFree(g->d_p);
@@ -336,6 +361,9 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
 tnlm_status tnlm_project(const tnlm_geometry *g, const float *vol, float *proj, void *stream)
 {
     if (!g || !vol || !proj) return arg_error("geometry, vol and proj must not be NULL");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(as_stream(stream), &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        ensure_coltab(const_cast<tnlm_geometry *>(g));  // the handle's tables are mutable state
     return launch_forward(g->kg, g->d_views, g->n_views_total, vol, nullptr, proj, nullptr, 0, as_stream(stream));
 }
 

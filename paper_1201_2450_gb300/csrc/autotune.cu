@@ -173,7 +173,11 @@ tnlm_status tnlm_autotune(tnlm_geometry *geo, const tnlm_params *p, int *choice,
     // projector block rows (mode 1: residual and partials, as in the FBS iteration)
     int best_by = kg.fwd_by;
     float best = FLT_MAX;
-    for (int by : {2, 4, 8}) {
+    // within the family that runs (the table walker once the handle's tables exist), so that the
+    // choice changes speed only
+    const bool tab = kg.coltab != nullptr && kg.fwd_by > 100;
+    for (int by : {2, 4, 8, 102, 104, 108}) {
+        if ((by > 100) != tab) continue;
         KGeom k = kg;
         k.fwd_by = by;
         float ms = 0.f;
@@ -280,15 +284,16 @@ tnlm_status tnlm_set_launch_shapes(tnlm_geometry *geo, int fwd_rows, int bp_cell
         set_error("geometry must not be NULL");
         return TNLM_ERR_ARG;
     }
-    if ((fwd_rows != 2 && fwd_rows != 4 && fwd_rows != 8) || (bp_cells != 4 && bp_cells != 8) ||
-        (bp_rows != 2 && bp_rows != 4)) {
-        set_error("launch shapes: projector rows in {2,4,8}, transpose cells in {4,8}, rows in {2,4} (got %d, %d, %d)",
+    if (!forward_shape_valid(fwd_rows) || (bp_cells != 4 && bp_cells != 8) || (bp_rows != 2 && bp_rows != 4)) {
+        set_error("launch shapes: projector in {2,4,8,102,104,108}, transpose cells in {4,8}, rows in {2,4} "
+                  "(got %d, %d, %d)",
                   fwd_rows, bp_cells, bp_rows);
         return TNLM_ERR_ARG;
     }
     geo->kg.fwd_by = fwd_rows;
     geo->kg.bp_ch = bp_cells;
     geo->kg.bp_by = bp_rows;
+    ensure_coltab(geo);  // a table shape builds the handle's tables now
     return TNLM_OK;
 }
 

@@ -247,6 +247,257 @@ __global__ void __launch_bounds__(kFwdBX *BY)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The table walker.  The rays of one detector column lie in one vertical
+// plane (their x and y coordinates along the ray parameter do not depend on
+// the detector row), so every row of the column crosses the same xy cells at
+// the same ray parameters.  k_coltab lays out that sequence once per
+// geometry handle -- entry k of (view, column): the ray parameter where the
+// ray leaves its k-th xy cell, and the cell's index y * nx + x -- and
+// k_forward_tab walks each row's ray through its column's entries, adding
+// only that row's z-plane crossings.  The walk has no branch on in-plane
+// crossings: the lanes of a warp are adjacent columns of one row, each
+// reading its own column's next entries (the tables interleave the columns,
+// so those reads are coalesced), and the z crossings, which depend on the
+// row alone, fall within an entry or two of each other across the warp.
+// ---------------------------------------------------------------------------
+
+constexpr int kColtabPad = 3;  // exit entry repeated after the last so reads ahead need no test
+
+// The in-plane part of the ray of detector column iu of view V, shared by
+// k_coltab and k_forward_tab (the same expressions as k_forward).
+struct ColumnRay {
+    float Dx, Dy, Ex, Ey, Gx, Gy, blo, bhi;
+    bool ok;
+    // a = the dominant in-plane axis (at most one b crossing per a-slab), b = the other
+    bool xa;
+    float Ea, Eb, Ga, Gb, iva, ivb, oa, ob, fa0, fb0, saf, sbf;
+    int na, nb, sa, sb, ia0, ib0, ia1, ib1, n_a, n_b;
+
+    __device__ __forceinline__ void init(const KGeom &G, const ViewGeom &V, int iu)
+    {
+        const float u = ((float)iu - G.uc) * G.du + G.u_off;
+        Dx = -G.sdd * V.c - u * V.s;
+        Dy = -G.sdd * V.s + u * V.c;
+        const float au = G.alpha0 * u;
+        Ex = (-au * V.s - G.b0x) * G.inv_dx;
+        Ey = (au * V.c - G.b0y) * G.inv_dy;
+        Gx = Dx * G.inv_dx;
+        Gy = Dy * G.inv_dy;
+        blo = -G.alpha0;
+        bhi = 1.f - G.alpha0;
+        ok = true;
+        slab_grid(Ex, Gx, G.nx, blo, bhi, ok);
+        slab_grid(Ey, Gy, G.ny, blo, bhi, ok);
+        ok = ok && blo < bhi;
+        n_a = n_b = 0;
+        if (!ok) return;
+        xa = fabsf(Gx) >= fabsf(Gy);
+        Ea = xa ? Ex : Ey;
+        Eb = xa ? Ey : Ex;
+        Ga = xa ? Gx : Gy;
+        Gb = xa ? Gy : Gx;
+        na = xa ? G.nx : G.ny;
+        nb = xa ? G.ny : G.nx;
+        sa = Ga > 0.f ? 1 : -1;
+        sb = Gb > 0.f ? 1 : -1;
+        iva = 1.0f / Ga;
+        ivb = Gb != 0.f ? 1.0f / Gb : 0.f;
+        oa = -Ea * iva;
+        ob = -Eb * ivb;
+        ia0 = clamp_floor(fmaf(blo, Ga, Ea), na);
+        ib0 = clamp_floor(fmaf(blo, Gb, Eb), nb);
+        ia1 = clamp_floor(fmaf(bhi, Ga, Ea), na);
+        ib1 = clamp_floor(fmaf(bhi, Gb, Eb), nb);
+        // interior planes crossed between the entry and exit cells, in walking order:
+        // a-plane m at fmaf(fa0 + sa m, iva, oa), b-plane k at fmaf(fb0 + sb k, ivb, ob)
+        n_a = abs(ia1 - ia0);
+        n_b = Gb != 0.f ? abs(ib1 - ib0) : 0;
+        fa0 = (float)(ia0 + (Ga > 0.f));
+        fb0 = (float)(ib0 + (Gb > 0.f));
+        saf = (float)sa;
+        sbf = (float)sb;
+    }
+    __device__ __forceinline__ float beta_a(int m) const { return fmaf(fmaf((float)m, saf, fa0), iva, oa); }
+    __device__ __forceinline__ float beta_b(int k) const { return fmaf(fmaf((float)k, sbf, fb0), ivb, ob); }
+    __device__ __forceinline__ int cell(int ia, int ib, int nx) const { return xa ? ib * nx + ia : ia * nx + ib; }
+    // entries of the column: one per interior plane crossed, and the exit
+    __device__ __forceinline__ int entries() const { return ok ? n_a + n_b + 1 : 0; }
+};
+
+// Entries of every (view, column): thread t of (view vg, column iu) places the
+// t-th plane crossing (a-planes first, then b-planes) at its rank in the merged
+// order, found by binary search over the other axis (ties: the a-plane first);
+// the thread with t == n_a + n_b writes the exit, and repeats it in the next
+// kColtabPad slots so that the walk can read ahead without bounds tests.
+// Layout: tab[(vg * kmax + k) * nu + iu], kmax = nx + ny - 1 + kColtabPad.
+__global__ void __launch_bounds__(128) k_coltab(KGeom G, const ViewGeom *__restrict__ views, float2 *__restrict__ tab,
+                                                int kmax)
+{
+    const int iu = blockIdx.y, vg = blockIdx.z;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    ColumnRay R;
+    R.init(G, views[vg], iu);
+    if (!R.ok || t > R.n_a + R.n_b) return;
+    float beta;
+    int e, ca, cb;
+    if (t == R.n_a + R.n_b) {
+        beta = R.bhi;
+        e = t;
+        ca = R.ia1;
+        cb = R.ib1;
+    } else if (t < R.n_a) {
+        // a-plane m: preceded by the b-planes crossed strictly before it
+        const int m = t;
+        beta = R.beta_a(m);
+        int lo = 0, hi = R.n_b;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (R.beta_b(mid) < beta) lo = mid + 1;
+            else hi = mid;
+        }
+        e = m + lo;
+        ca = R.ia0 + R.sa * m;
+        cb = R.ib0 + R.sb * lo;
+    } else {
+        // b-plane k: preceded by the a-planes crossed at or before it
+        const int k = t - R.n_a;
+        beta = R.beta_b(k);
+        int lo = 0, hi = R.n_a;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (R.beta_a(mid) <= beta) lo = mid + 1;
+            else hi = mid;
+        }
+        e = k + lo;
+        ca = R.ia0 + R.sa * lo;
+        cb = R.ib0 + R.sb * k;
+    }
+    // the cell before this crossing; the crossing clamped to the column's extent
+    const float2 ent = make_float2(fminf(fmaxf(beta, R.blo), R.bhi), __int_as_float(R.cell(ca, cb, G.nx)));
+    tab[((long long)vg * kmax + e) * G.nu + iu] = ent;
+    if (t == R.n_a + R.n_b)
+        for (int q = 1; q <= kColtabPad; ++q) tab[((long long)vg * kmax + e + q) * G.nu + iu] = ent;
+}
+
+
+// One ray per thread (block: 32 adjacent columns x BY rows of one view), walked
+// through its column's table two entries per step, the next two entries in
+// flight while the current pair is summed; a z crossing splits an entry's
+// segment (the loop takes any number of them, so no geometry condition
+// applies).
+template <int MODE, int BY, class T>
+__global__ void __launch_bounds__(kFwdBX *BY)
+    k_forward_tab(KGeom G, const ViewGeom *__restrict__ views, const T *__restrict__ vol,
+                  const T *__restrict__ y, float *__restrict__ out, double *__restrict__ partials)
+{
+    __shared__ double ws[BY];
+    const int iu = blockIdx.x * kFwdBX + threadIdx.x;
+    const int iv = blockIdx.y * BY + threadIdx.y;
+    const int vg = blockIdx.z;
+    double r2 = 0.0;
+    if (iu < G.nu && iv < G.nv) {
+        const ViewGeom V = views[vg];
+        ColumnRay R;
+        R.init(G, V, iu);
+        const float v = ((float)iv - G.vc) * G.dv + G.v_off;
+        const float Dz = v;
+        const float len = sqrtf(R.Dx * R.Dx + R.Dy * R.Dy + Dz * Dz);
+        const float Ez = (G.alpha0 * v - G.b0z) * G.inv_dz;
+        const float Gz = Dz * G.inv_dz;
+        float blo = R.blo, bhi = R.bhi;
+        bool ok = R.ok;
+        slab_grid(Ez, Gz, G.nz, blo, bhi, ok);
+        float acc = 0.f;
+        if (ok && blo < bhi) {
+            const int sc = Gz > 0.f ? 1 : -1;
+            const float ivc = Gz != 0.f ? 1.0f / Gz : 0.f, oc = -Ez * ivc, scf = (float)sc;
+            const int ic0 = clamp_floor(fmaf(blo, Gz, Ez), G.nz), ic1 = clamp_floor(fmaf(bhi, Gz, Ez), G.nz);
+            int nzc = Gz != 0.f ? abs(ic1 - ic0) : 0;  // z planes crossed inside the volume
+            float fc = (float)(ic0 + (Gz > 0.f));
+            float bc = nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
+            const int zstep = sc * G.nx * G.ny;
+            const T *__restrict__ fp = vol + (long long)V.phase * G.nvox + (long long)ic0 * G.nx * G.ny;
+            const long long st = G.nu;  // entry stride in the interleaved tables
+            const float2 *__restrict__ tc = G.coltab + (long long)vg * G.coltab_kmax * st + iu;
+            const int K = R.entries();
+            // this row's entries: the first that ends after blo .. the first that ends at or after bhi
+            // (rows inside the volume's z range enter and leave through its sides: all entries)
+            int k0 = 0, k1 = K - 1;
+            if (blo > R.blo) {
+                int lo = 0, hi = K - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(tc + mid * st).x > blo) hi = mid;
+                    else lo = mid + 1;
+                }
+                k0 = lo;
+            }
+            if (bhi < R.bhi) {
+                int lo = k0, hi = K - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(tc + mid * st).x >= bhi) hi = mid;
+                    else lo = mid + 1;
+                }
+                k1 = lo;
+            }
+            float bcur = blo;
+            const float2 *__restrict__ tp = tc + k0 * st;
+            float2 t0 = __ldg(tp), t1 = __ldg(tp + st);
+            for (int k = k0; k <= k1; k += 2) {
+                tp += 2 * st;
+                const float2 n0 = __ldg(tp), n1 = __ldg(tp + st);  // entries k+2, k+3 (padding past the exit)
+                float f0 = ldg_v(fp + __float_as_int(t0.y));
+                float f1 = ldg_v(fp + __float_as_int(t1.y));
+                float e = fminf(t0.x, bhi);
+                if (bc < e) {
+                    do {  // z crossings inside entry k's segment
+                        acc = fmaf(f0, bc - bcur, acc);
+                        bcur = bc;
+                        fp += zstep;
+                        f0 = ldg_v(fp + __float_as_int(t0.y));
+                        fc += scf;
+                        bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
+                    } while (bc < e);
+                    f1 = ldg_v(fp + __float_as_int(t1.y));
+                }
+                acc = fmaf(f0, e - bcur, acc);
+                bcur = e;
+                if (k < k1) {
+                    e = fminf(t1.x, bhi);
+                    while (bc < e) {  // z crossings inside entry k+1's segment
+                        acc = fmaf(f1, bc - bcur, acc);
+                        bcur = bc;
+                        fp += zstep;
+                        f1 = ldg_v(fp + __float_as_int(t1.y));
+                        fc += scf;
+                        bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
+                    }
+                    acc = fmaf(f1, e - bcur, acc);
+                    bcur = e;
+                }
+                t0 = n0;
+                t1 = n1;
+            }
+        }
+        const float pf = acc * len;
+        const long long o = ((long long)vg * G.nv + iv) * G.nu + iu;
+        if (MODE == 0) {
+            out[o] = pf;
+        } else {
+            const float r = pf - ldg_v(y + o);
+            out[o] = r * len;  // scaled residual consumed by the transpose
+            r2 = (double)r * (double)r;
+        }
+    }
+    if (MODE == 1) {
+        const double s = block_sum_warps<BY>(r2, ws);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 template <bool SCALED, class T>
 __global__ void __launch_bounds__(kBpBX *kBpBY)
     k_backproject(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
@@ -563,14 +814,48 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
 
 }  // namespace
 
+// Projector launch shape code: 2, 4 or 8 = the slab walker k_forward with blocks of 32 x that
+// many rows; 102, 104 or 108 = the table walker k_forward_tab with blocks of 32 x 2, 4 or 8 rows,
+// once the handle's column tables exist (else the slab walker with 4 rows).
+bool forward_shape_valid(int code)
+{
+    return code == 2 || code == 4 || code == 8 || code == 102 || code == 104 || code == 108;
+}
+
+static int effective_forward_shape(const KGeom &kg)
+{
+    return (kg.fwd_by > 100 && !kg.coltab) ? 4 : kg.fwd_by;
+}
+
 long long forward_blocks(const KGeom &kg, int n_views_total)
 {
-    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + kg.fwd_by - 1) / kg.fwd_by) * n_views_total;
+    const int rows = effective_forward_shape(kg) % 100;
+    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + rows - 1) / rows) * n_views_total;
 }
 
 long long forward_blocks_max(const KGeom &kg, int n_views_total)
 {
-    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + 1) / 2) * n_views_total;  // smallest BY = 2
+    return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + 1) / 2) * n_views_total;  // fewest rows: 2
+}
+
+int coltab_kmax(const KGeom &kg) { return kg.nx + kg.ny - 1 + kColtabPad; }
+
+size_t coltab_entries(const KGeom &kg, int n_views_total)
+{
+    return (size_t)n_views_total * (size_t)coltab_kmax(kg) * (size_t)kg.nu;
+}
+
+tnlm_status build_coltab(const KGeom &kg, const ViewGeom *views, int n_views_total, float2 *tab, cudaStream_t st)
+{
+    const int kmax = coltab_kmax(kg);
+    if (kg.nu > 65535) {
+        set_error("column tables need nu <= 65535 (got %d)", kg.nu);
+        return TNLM_ERR_ARG;
+    }
+    dim3 grid((kmax + 127) / 128, kg.nu, n_views_total);
+    k_coltab<<<grid, 128, 0, st>>>(kg, views, tab, kmax);
+    TNLM_TRY_CUDA(cudaGetLastError());
+    return TNLM_OK;
 }
 
 template <int MODE, int BY, class T>
@@ -581,23 +866,39 @@ static void launch_forward_by(const KGeom &kg, const ViewGeom *views, int n_view
     k_forward<MODE, BY, T><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views, vol, y, out, partials);
 }
 
+template <int MODE, int BY, class T>
+static void launch_forward_tab(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol, const T *y,
+                               float *out, double *partials, cudaStream_t st)
+{
+    dim3 grid((kg.nu + kFwdBX - 1) / kFwdBX, (kg.nv + BY - 1) / BY, n_views_total);
+    k_forward_tab<MODE, BY, T><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views, vol, y, out, partials);
+}
+
+template <int MODE, class T>
+static void launch_forward_mode(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol, const T *y,
+                                float *out, double *partials, cudaStream_t st)
+{
+    switch (effective_forward_shape(kg)) {
+    case 2: launch_forward_by<MODE, 2, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    case 8: launch_forward_by<MODE, 8, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    case 102: launch_forward_tab<MODE, 2, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    case 104: launch_forward_tab<MODE, 4, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    case 108: launch_forward_tab<MODE, 8, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    default: launch_forward_by<MODE, 4, T>(kg, views, n_views_total, vol, y, out, partials, st); break;
+    }
+}
+
 template <class T>
 static tnlm_status launch_forward_t(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol,
                                     const T *y, float *out, double *partials, int mode, cudaStream_t st)
 {
-    if (kg.fwd_by != 2 && kg.fwd_by != 4 && kg.fwd_by != 8) {
-        set_error("projector block rows must be 2, 4 or 8 (got %d)", kg.fwd_by);
+    if (!forward_shape_valid(kg.fwd_by)) {
+        set_error("projector launch shape must be 2, 4, 8 (slab walker) or 102, 104, 108 (table walker) (got %d)",
+                  kg.fwd_by);
         return TNLM_ERR_ARG;
     }
-    if (mode == 0) {
-        if (kg.fwd_by == 2) launch_forward_by<0, 2, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
-        else if (kg.fwd_by == 4) launch_forward_by<0, 4, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
-        else launch_forward_by<0, 8, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
-    } else {
-        if (kg.fwd_by == 2) launch_forward_by<1, 2, T>(kg, views, n_views_total, vol, y, out, partials, st);
-        else if (kg.fwd_by == 4) launch_forward_by<1, 4, T>(kg, views, n_views_total, vol, y, out, partials, st);
-        else launch_forward_by<1, 8, T>(kg, views, n_views_total, vol, y, out, partials, st);
-    }
+    if (mode == 0) launch_forward_mode<0, T>(kg, views, n_views_total, vol, nullptr, out, nullptr, st);
+    else launch_forward_mode<1, T>(kg, views, n_views_total, vol, y, out, partials, st);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
 }

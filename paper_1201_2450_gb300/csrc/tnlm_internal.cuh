@@ -27,9 +27,12 @@ struct KGeom {
     long long nvox;          // nx*ny*nz
     long long npix;          // nu*nv
     // launch shapes (defaults 4, 4, 8; chosen by tnlm_autotune)
-    int fwd_by;              // projector block rows: 2, 4 or 8
+    int fwd_by;              // projector shape: 2, 4, 8 (slab walker rows) or 102, 104, 108 (table walker)
     int bp_by;               // band transpose block rows: 2 or 4
     int bp_ch;               // band transpose z cells per thread: 4 or 8
+    // column tables of the table walker (owned by the geometry handle; null until built)
+    const float2 *coltab;    // [views][coltab_kmax][nu]: (ray parameter leaving the xy cell, cell index bits)
+    int coltab_kmax;
 };
 
 // One projection view: rotation and owning phase.
@@ -69,6 +72,11 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
                            const __half *y, float *out, double *partials, int mode, cudaStream_t st);
 long long forward_blocks(const KGeom &kg, int n_views_total);
 long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
+bool forward_shape_valid(int code);  // projector launch shape code (KGeom::fwd_by)
+// column tables of the table walker: entries per view and column (nx + ny - 1 + padding), total, build
+int coltab_kmax(const KGeom &kg);
+size_t coltab_entries(const KGeom &kg, int n_views_total);
+tnlm_status build_coltab(const KGeom &kg, const ViewGeom *views, int n_views_total, float2 *tab, cudaStream_t st);
 
 // vout = beta * vin + alpha * P^T proj.  scaled: proj already multiplied by
 // the ray length |source -> pixel| (the residual form written by mode 1).
@@ -249,6 +257,8 @@ struct tnlm_geometry {
     long long part_len = 0;
     double *d_scalars = nullptr;      // reduction results
     float *d_pref = nullptr;          // column prefix sums for the transpose (prefix_floats)
+    float2 *d_coltab = nullptr;       // column tables of the table projector (coltab_entries)
+    bool coltab_failed = false;       // their allocation failed once: the slab walker runs
     // CGLS workspace (allocated on first use)
     float *d_q = nullptr;             // sum(n_views) * npix
     float *d_s = nullptr;             // np * nvox
@@ -270,5 +280,9 @@ namespace tnlm {
 // the band-transpose prefix array (nullptr when the geometry does not admit
 // that transpose or the allocation failed).
 tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars);
+// Column tables of the table projector: built on first use (synchronising the
+// device, so never during stream capture); on allocation failure the slab
+// walker runs instead (the same model, FP32 rounding of its own).
+void ensure_coltab(tnlm_geometry *g);
 float *prefix_workspace(tnlm_geometry *g);
 }  // namespace tnlm

@@ -989,6 +989,7 @@ def test_out_of_memory_paths_and_recovery(ora):
     p = tnlm.Params(d=1, M=2, h=0.02, mu=1.0, tau=1e-3, n_outer=2)
     G = tnlm.Geometry(pb.geom)
     f = torch.zeros(G.vol_shape, device="cuda")
+    tnlm.tnlm_project(G, f)  # builds the handle's projector tables first
     assert lib.tnlm_test_fail_allocations(1) == 0
     with pytest.raises(tnlm.TnlmError) as e:
         tnlm.tnlm_reconstruct(G, cuda(pb.y.numpy()), f, p)
@@ -1000,6 +1001,14 @@ def test_out_of_memory_paths_and_recovery(ora):
     tnlm.tnlm_reconstruct(G2, cuda(pb.y.numpy()), f2, p)
     torch.cuda.synchronize()
     assert torch.equal(f, f2)
+    # projector tables that cannot be allocated: the slab walker runs, equal to the oracle
+    G4 = tnlm.Geometry(GEOMS["ragged_uneven"])
+    x = synth.uniform(G4.vol_shape, 78)
+    assert lib.tnlm_test_fail_allocations(1) == 0
+    px = tnlm.tnlm_project(G4, cuda(x)).cpu().numpy()
+    assert lib.tnlm_test_fail_allocations(0) == 0
+    assert rel_l2(px, ora.project(ora.Geometry(GEOMS["ragged_uneven"]), x)) <= RTOL
+    G4.close()
     g = cuda(synth.smooth_volume((3, 8, 12, 16), 5))
     pe = tnlm.Params(d=1, M=1, h=0.02, mu=1.0, n_outer=3, clip_nonneg=0)
     assert lib.tnlm_test_fail_allocations(1) == 0

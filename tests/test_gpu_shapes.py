@@ -28,9 +28,13 @@ def test_projector_and_transpose_shapes_bitwise_equal(name):
     x = cuda(synth.uniform(G.vol_shape, 300))
     r = cuda(synth.uniform(G.proj_shape, 301))
     outs_p, outs_b = [], []
-    for rows in (2, 4, 8):
+    outs_t = []
+    for rows in (2, 4, 8):  # the slab walker
         tnlm.tnlm_set_launch_shapes(G, rows, 8, 4)
         outs_p.append(tnlm.tnlm_project(G, x))
+    for rows in (102, 104, 108):  # the table walker
+        tnlm.tnlm_set_launch_shapes(G, rows, 8, 4)
+        outs_t.append(tnlm.tnlm_project(G, x))
     for cells in (4, 8):
         for rows in (2, 4):
             tnlm.tnlm_set_launch_shapes(G, 4, cells, rows)
@@ -38,8 +42,38 @@ def test_projector_and_transpose_shapes_bitwise_equal(name):
     torch.cuda.synchronize()
     for o in outs_p[1:]:
         assert torch.equal(o, outs_p[0])
+    for o in outs_t[1:]:
+        assert torch.equal(o, outs_t[0])
+    # the two walkers agree to FP32 rounding
+    d = (outs_t[0].double() - outs_p[0].double()).norm() / outs_p[0].double().norm()
+    assert float(d) <= 1e-6
     for o in outs_b[1:]:
         assert torch.equal(o, outs_b[0])
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_projector_shapes_residual_path_bitwise_equal(name):
+    """The fused residual (FP32 and BF16 storage) through one TNLM-R iteration:
+    the same image for every projector shape of one walker."""
+    G = tnlm.Geometry(GEOMS[name])
+    y = cuda(synth.uniform(G.proj_shape, 302) * 0.3)
+    f0 = cuda(synth.smooth_volume(G.vol_shape, 303))
+    p = tnlm.Params(d=1, M=2, h=0.02, mu=0.8, tau=1e-4, n_outer=1)
+    for family in ((2, 4, 8), (102, 104, 108)):
+        outs, outs16 = [], []
+        for rows in family:
+            tnlm.tnlm_set_launch_shapes(G, rows, 8, 4)
+            f = f0.clone()
+            tnlm.tnlm_reconstruct(G, y, f, p)
+            outs.append(f)
+            f16 = f0.bfloat16()
+            tnlm.tnlm_reconstruct_bf16(G, y.bfloat16(), f16, p)
+            outs16.append(f16)
+        torch.cuda.synchronize()
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        for o in outs16[1:]:
+            assert torch.equal(o, outs16[0])
 
 
 @pytest.mark.parametrize("d, M", [(1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3)])
@@ -73,7 +107,7 @@ def test_autotune_keeps_results():
     tnlm.tnlm_reconstruct(G, y, before, p)
     try:
         ch = tnlm.tnlm_autotune(G, p)
-        assert ch["projector_rows"] in (2, 4, 8)
+        assert ch["projector_rows"] in (102, 104, 108)
         assert ch["transpose_cells"] in (4, 8) and ch["transpose_rows"] in (2, 4)
         assert 0 <= ch["sweep_shape"] < 4
         after = cuda(f0)
