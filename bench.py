@@ -46,11 +46,12 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # each kernel on this workload, with the SHA-256 of the kernel source it was
 # measured on; a changed source invalidates the figure (reported as null).
 NCU_TRAFFIC = {
-    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload;
-    # the transpose stage is the column scan (its own earlier capture, source unchanged) plus the band kernel
-    "k_forward": {"bytes_per_launch": int((273.283328e6 + 147.755776e6) * 10 / 6), "source_sha": "a988298ded5a6752"},
-    "k_backproject": {"bytes_per_launch": int((169.895936e6 + 284.310784e6 + 557.578752e6 + 93.134080e6) * 10 / 6),
-                      "source_sha": "a988298ded5a6752"},
+    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload; the
+    # projector stage is the bricked copy plus the table walk, the transpose stage the column scan plus the bands
+    "k_forward": {"bytes_per_launch": int((100.747008e6 + 48.406272e6 + 595.252736e6 + 162.568448e6) * 10 / 6),
+                  "source_sha": "b253635451a9a7ba"},
+    "k_backproject": {"bytes_per_launch": int((169.893632e6 + 284.609024e6 + 558.020096e6 + 93.149184e6) * 10 / 6),
+                      "source_sha": "35125fe705d5a4a4"},
     "k_sweep": {"bytes_per_launch": int((160.676608e6 + 84.272896e6) * 10 / 6), "source_sha": "5c1e717465e6a4bc"},
 }
 
@@ -60,7 +61,7 @@ def _src_sha(fname: str) -> str:
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-KERNEL_SRC = {"k_forward": "projector.cu", "k_backproject": "projector.cu", "k_sweep": "sweep_box.cuh"}
+KERNEL_SRC = {"k_forward": "projector.cu", "k_backproject": "transpose.cu", "k_sweep": "sweep_box.cuh"}
 
 
 def measured_peaks() -> dict:
@@ -174,6 +175,11 @@ def projection_nnz(desc: dict, device="cuda") -> int:
 # plane by one FMA), per in-plane (b) crossing 3 more, per z (c) crossing 7 (its segment and the next
 # z plane); so per ray 12 (1 + |da|) + 3 |db| + 7 |dc| with da, db, dc the cell steps along each axis.
 K1_FLOP_SLAB, K1_FLOP_B, K1_FLOP_C = 12, 3, 7
+# FP32 operations of the table walk (the default projector), counted from its source: per xy-table
+# entry 4 (the entry's end clamped to the ray's exit, its segment length and FMA), per z crossing 6
+# (its segment length and FMA, the next z plane by an add and one FMA); so per ray
+# 4 (1 + |dx| + |dy|) + 6 |dz|.  The tables themselves are built once per geometry, not per launch.
+K1_TAB_FLOP_ENTRY, K1_TAB_FLOP_C = 4, 6
 # FP32 operations of the band transpose per non-zero of P, counted from its source on this geometry:
 # per (column of 8 cells, view, pixel column) about 46 for the chord and row maps and 26 per cell
 # boundary (its row images, the band row split, the full-row prefix difference), 280 in all, plus
@@ -182,16 +188,17 @@ K1_FLOP_SLAB, K1_FLOP_B, K1_FLOP_C = 12, 3, 7
 K2_FLOP_PER_NNZ = 7.7
 
 
-def projection_counts(desc: dict, device="cuda") -> tuple[int, int]:
-    """(nnz(P), FP32 operations of the slab walk), exact per ray from the
-    entry and exit cells along each axis; the dominant axis is x or y (the
-    steeper of the two, z when steeper still), as in the kernel."""
+def projection_counts(desc: dict, device="cuda") -> tuple[int, int, int]:
+    """(nnz(P), FP32 operations of the slab walk, of the table walk), exact
+    per ray from the entry and exit cells along each axis; the slab walk's
+    dominant axis is x or y (the steeper of the two, z when steeper still),
+    as in the kernel."""
     nu, nv = desc["nu"], desc["nv"]
     dev = torch.device(device)
     u = (torch.arange(nu, device=dev, dtype=torch.float64) - 0.5 * (nu - 1)) * desc["du"] + desc["u_off"]
     v = (torch.arange(nv, device=dev, dtype=torch.float64) - 0.5 * (nv - 1)) * desc["dv"] + desc["v_off"]
     V, U = torch.meshgrid(v, u, indexing="ij")
-    flops = 0
+    flops = flops_tab = 0
     n = [desc["nx"], desc["ny"], desc["nz"]]
     w = [desc["dx"], desc["dy"], desc["dz"]]
     b0 = [desc["cx"] - 0.5 * n[0] * w[0], desc["cy"] - 0.5 * n[1] * w[1], desc["cz"] - 0.5 * n[2] * w[2]]
@@ -224,10 +231,12 @@ def projection_counts(desc: dict, device="cuda") -> tuple[int, int]:
         sb = torch.where(xa, steps[1], steps[0])
         sc = torch.where(zdom, steps[1], steps[2])
         fl = K1_FLOP_SLAB * (1 + sa) + K1_FLOP_B * sb + K1_FLOP_C * sc
+        ft = K1_TAB_FLOP_ENTRY * (1 + steps[0] + steps[1]) + K1_TAB_FLOP_C * steps[2]
         zero = torch.zeros_like(cnt)
         total += int(torch.where(hit, cnt, zero).sum().item())
         flops += int(torch.where(hit, fl, zero).sum().item())
-    return total, flops
+        flops_tab += int(torch.where(hit, ft, zero).sum().item())
+    return total, flops, flops_tab
 
 
 # FP32 operations per pair evaluation of the sweep (the hot-path analysis's per-unit figure):
@@ -375,8 +384,10 @@ def run_ours(args, rank, world, local):
     if t and t.get("source_sha") == _src_sha(KERNEL_SRC[dom]) and cfg.n_phases == 10:
         traffic = t["bytes_per_launch"]
     # the three kernels are bound by FP32 / integer issue, not HBM: roofline against the FP32 peak
-    nnz, k1_flop = projection_counts(pb.geom)
-    work = {"k_forward": k1_flop, "k_backproject": K2_FLOP_PER_NNZ * nnz,
+    nnz, k1_slab, k1_tab = projection_counts(pb.geom)
+    in_use = tnlm.tnlm_get_launch_shapes(geom)
+    k1_table = in_use["projector_rows"] > 100
+    work = {"k_forward": k1_tab if k1_table else k1_slab, "k_backproject": K2_FLOP_PER_NNZ * nnz,
             "k_sweep": sweep_ops_per_pair(cfg.d) * sweep_pairs(cfg)}
     peak_t = cpk["fp32_tflops"]
     alu = {n: {"algorithmic_tflop": round(work[n] / 1e12, 4),
@@ -401,8 +412,9 @@ def run_ours(args, rank, world, local):
                    "step": "one FBS iteration (projection+residual, transpose+gradient step, weights+Gauss-Jacobi+clip)",
                    "l2": "inputs larger than L2 (y 283 MB, f 168 MB), no flush",
                    "parallelism": f"replicas x{world} (independent reconstructions)",
-                   "launch_shapes": shapes if shapes else "defaults (projector rows 4, transpose 8 cells x 4 rows, "
-                                                         "sweep shape 0)"},
+                   "launch_shapes": dict(in_use, sweep_shape=shapes["sweep_shape"] if shapes else "default",
+                                         projector_walker="table" if k1_table else "slab",
+                                         autotuned=shapes is not None)},
         "tnlm_voxel_updates_per_s": round(nvox_upd / sweep_s, 1),
         "projector_segments_per_s": round(nnz / (per_launch_ms["k_forward"] / 1e3), 1),
         "transpose_segments_per_s": round(nnz / (per_launch_ms["k_backproject"] / 1e3), 1),
@@ -413,8 +425,9 @@ def run_ours(args, rank, world, local):
         "compute_peaks": cpk,
         "roofline": roofline,
         "clocks": clocks,
-        # per step: k_forward, the transpose stage (k_colscan + k_backproject_bands on this workload), k_sweep_box
-        "gpu_launches": int(stage_n[0] + 2 * stage_n[1] + stage_n[2]),
+        # per step: the projector stage (k_brick + k_forward_tab, or k_forward alone), the transpose stage
+        # (k_colscan + k_backproject_bands on this workload), k_sweep_box
+        "gpu_launches": int(stage_n[0] * (2 if k1_table else 1) + 2 * stage_n[1] + stage_n[2]),
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "variants": variants,

@@ -104,7 +104,10 @@ void tnlm_destroy_geometry(tnlm_geometry *geom);
  * (Siddon, the paper's ref. 40, used for the projections of Sec. 2.5) of
  * each source->pixel-centre segment through the voxel cells of that view's
  * phase image (the operator P_i of Eq. 1).  vol: [N_p][nz][ny][nx]; proj:
- * [sum n_views][nv][nu]; they must not overlap. */
+ * [sum n_views][nv][nu]; they must not overlap.  With the table walker (the
+ * default projector shape, see tnlm_autotune) the call stages vol in the
+ * handle's workspace, so projections through one handle must not overlap on
+ * the GPU (issue them on one stream, or serialise them). */
 tnlm_status tnlm_project(const tnlm_geometry *geom, const float *vol, float *proj, void *stream);
 
 /* vol = beta * vol + alpha * P^T proj: the exact transpose of tnlm_project,
@@ -374,10 +377,13 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * crossings) or 102, 104 or 108 (the table walker: blocks of 32 x 2, 4 or 8
  * pixels; the xy cells every detector column crosses are laid out once per
  * handle in device memory, views x (nx + ny + 2) x nu entries of 8 bytes,
- * and each ray adds only its own z crossings).  A new handle starts at 104;
- * its tables are built, synchronising the device, by the first call that
- * projects (or by tnlm_set_launch_shapes), never during a stream capture; if
- * they cannot be allocated the slab walker with 4 rows runs.  The two
+ * and each ray adds only its own z crossings, reading a copy of the volume
+ * that each projection first writes into the handle's workspace with its
+ * z slices in 4 x 8 (x, y) bricks: N_p x nz x ceil(nx/4) x ceil(ny/8) x 32
+ * voxels of 4 bytes).  A new handle starts at 104; its tables are built,
+ * synchronising the device, by the first call that projects (or by
+ * tnlm_set_launch_shapes), never during a stream capture; if the tables or
+ * the copy cannot be allocated the slab walker with 4 rows runs.  The two
  * walkers compute the same exact model but do not round alike, so the
  * autotuner chooses within the walker that runs.
  * tnlm_set_launch_shapes / tnlm_set_sweep_shape set a shape directly
@@ -389,6 +395,10 @@ tnlm_status tnlm_autotune_sweep(int nx, int ny, int nz, int n_phases, int d, int
                                 void *stream);
 tnlm_status tnlm_set_launch_shapes(tnlm_geometry *geom, int projector_rows, int transpose_cells, int transpose_rows);
 tnlm_status tnlm_set_sweep_shape(int d, int M, int bf16, int shape);
+/* The handle's launch shapes as they run now (host array of 3): the
+ * projector code (4 while a table shape waits for, or could not allocate,
+ * its tables), the transpose cells and rows.  TNLM_ERR_ARG for NULL. */
+tnlm_status tnlm_get_launch_shapes(const tnlm_geometry *geom, int shapes[3]);
 
 /* FDK reconstruction (Feldkamp, Davis and Kress, the paper's ref. 16), the
  * initial value f^(0) of TNLM-R and the input g of TNLM-E (Sec. 2.2-2.3):

@@ -29,7 +29,7 @@ __all__ = [
     "tnlm_weights", "tnlm_gauss_jacobi", "tnlm_reconstruct", "tnlm_enhance", "tnlm_enhance_noalloc",
     "tnlm_operator_norm", "tnlm_cgls", "tnlm_fdk", "tnlm_gauss_jacobi_bf16", "tnlm_enhance_bf16",
     "tnlm_energy_grad", "tnlm_energy_grad_weights", "tnlm_energy_grad_bf16", "TNLMEnergy", "tnlm_reconstruct_batch", "BatchPlan", "tnlm_reconstruct_bf16",
-    "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_set_sweep_shape",
+    "tnlm_autotune", "tnlm_autotune_sweep", "tnlm_set_launch_shapes", "tnlm_get_launch_shapes", "tnlm_set_sweep_shape",
     "reconstruct_host", "library_path", "tnlm_peak_probe", "tnlm_gauss_jacobi_range", "tnlm_p1",
     "tnlm_reconstruct_fp16", "tnlm_enhance_fp16", "tnlm_gauss_jacobi_fp16", "tnlm_energy_grad_fp16",
     "tnlm_gauss_jacobi_pairs",
@@ -136,6 +136,7 @@ def _load():
             "tnlm_autotune": (i, [vp, C.POINTER(_Params), C.POINTER(C.c_int), vp]),
             "tnlm_autotune_sweep": (i, [i, i, i, i, i, i, f, i, C.POINTER(C.c_int), vp]),
             "tnlm_set_launch_shapes": (i, [vp, i, i, i]),
+            "tnlm_get_launch_shapes": (i, [vp, C.POINTER(C.c_int)]),
             "tnlm_set_sweep_shape": (i, [i, i, i, i]),
             "tnlm_enhance_bf16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_enhance_fp16": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
@@ -410,6 +411,14 @@ def tnlm_autotune_sweep(shape, d: int, M: int, h: float, bf16: bool = False, str
 def tnlm_set_launch_shapes(geom: Geometry, projector_rows: int, transpose_cells: int, transpose_rows: int):
     _check(_load().tnlm_set_launch_shapes(geom.handle, projector_rows, transpose_cells, transpose_rows),
            "tnlm_set_launch_shapes")
+
+
+def tnlm_get_launch_shapes(geom: Geometry) -> dict:
+    """The handle's launch shapes as they run now (projector code 4 while a
+    table shape has no tables)."""
+    out = (C.c_int * 3)()
+    _check(_load().tnlm_get_launch_shapes(geom.handle, out), "tnlm_get_launch_shapes")
+    return {"projector_rows": out[0], "transpose_cells": out[1], "transpose_rows": out[2]}
 
 
 def tnlm_set_sweep_shape(d: int, M: int, bf16: bool, shape: int, fp16: bool = False):

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtnlm.so")
-SOURCES = ["sweep_box_v0.cu", "sweep_box_v1.cu", "sweep_box_v2.cu", "sweep_box_v3.cu", "projector.cu", "tnlm_sweep.cu",
+SOURCES = ["sweep_box_v0.cu", "sweep_box_v1.cu", "sweep_box_v2.cu", "sweep_box_v3.cu", "projector.cu", "transpose.cu", "tnlm_sweep.cu",
            "reduce.cu", "api.cu", "noalloc.cu", "cgls.cu", "fdk.cu", "energy.cu", "energy_box.cu", "autotune.cu", "peaks.cu", "sweep_pairs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -66,21 +66,26 @@ void ensure_coltab(tnlm_geometry *g)
 {
     if (g->d_coltab || g->coltab_failed || g->kg.fwd_by < 100) return;
     const size_t n = coltab_entries(g->kg, g->n_views_total);
-    if (forced_alloc_failure() || cudaMalloc(reinterpret_cast<void **>(&g->d_coltab), sizeof(float2) * n) != cudaSuccess) {
+    auto give_up = [g] {
         cudaGetLastError();
+        cudaFree(g->d_coltab);
+        cudaFree(g->d_volb);
         g->d_coltab = nullptr;
+        g->d_volb = nullptr;
         g->coltab_failed = true;
+    };
+    if (forced_alloc_failure() || cudaMalloc(reinterpret_cast<void **>(&g->d_coltab), sizeof(float2) * n) != cudaSuccess ||
+        cudaMalloc(&g->d_volb, brick_bytes(g->kg)) != cudaSuccess) {
+        give_up();
         return;
     }
     if (build_coltab(g->kg, g->d_views, g->n_views_total, g->d_coltab, cudaStreamLegacy) != TNLM_OK ||
         cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(g->d_coltab);
-        g->d_coltab = nullptr;
-        g->coltab_failed = true;
+        give_up();
         return;
     }
     g->kg.coltab = g->d_coltab;
+    g->kg.volb = g->d_volb;
 }
 
 tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars)
@@ -304,6 +309,8 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc *desc, tnlm_geometry *
     k.fwd_by = 104;  // the table projector once its tables are built (the slab walker until then)
     k.coltab = nullptr;
     k.coltab_kmax = coltab_kmax(k);
+    k.volb = nullptr;
+    k.brick_slice = brick_slice(d.nx, d.ny);
     g->n_views_total = (int)total;
     g->n_views.assign(d.n_views, d.n_views + d.n_phases);
     g->angles.assign(d.angles_rad, d.angles_rad + total);
@@ -347,6 +354,7 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_scalars);
     cudaFree(g->d_pref);
     cudaFree(g->d_coltab);
+    cudaFree(g->d_volb);
     cudaFree(g->d_q);
     cudaFree(g->d_s);
     cudaFree(g->d_p);

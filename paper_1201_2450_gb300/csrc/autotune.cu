@@ -297,6 +297,18 @@ tnlm_status tnlm_set_launch_shapes(tnlm_geometry *geo, int fwd_rows, int bp_cell
     return TNLM_OK;
 }
 
+tnlm_status tnlm_get_launch_shapes(const tnlm_geometry *geo, int shapes[3])
+{
+    if (!geo || !shapes) {
+        set_error("geometry and shapes must not be NULL");
+        return TNLM_ERR_ARG;
+    }
+    shapes[0] = forward_shape_in_use(geo->kg);
+    shapes[1] = geo->kg.bp_ch;
+    shapes[2] = geo->kg.bp_by;
+    return TNLM_OK;
+}
+
 tnlm_status tnlm_set_sweep_shape(int d, int M, int bf16, int shape)
 {
     if (d < 0 || d > 3 || M < 0 || M > 4 || shape < 0 || shape >= kBoxShapes) {

@@ -31,8 +31,13 @@ struct KGeom {
     int bp_by;               // band transpose block rows: 2 or 4
     int bp_ch;               // band transpose z cells per thread: 4 or 8
     // column tables of the table walker (owned by the geometry handle; null until built)
-    const float2 *coltab;    // [views][coltab_kmax][nu]: (ray parameter leaving the xy cell, cell index bits)
+    const float2 *coltab;    // [views][coltab_kmax][nu]: (ray parameter leaving the xy cell, brick offset bits)
     int coltab_kmax;
+    // the table walker's copy of the volume, each z slice laid out in 4 x 8 (x, y) bricks of 32
+    // voxels (x fastest inside a brick, bricks x-major): [N_p][nz][brick_slice] elements of the
+    // projected volume's type, written by the projector launch itself (null until built)
+    void *volb;
+    long long brick_slice;   // ceil(nx / 4) * ceil(ny / 8) * 32
 };
 
 // One projection view: rotation and owning phase.
@@ -73,9 +78,12 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
 long long forward_blocks(const KGeom &kg, int n_views_total);
 long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
 bool forward_shape_valid(int code);  // projector launch shape code (KGeom::fwd_by)
+int forward_shape_in_use(const KGeom &kg);  // the code that runs: the slab walker's 4 without tables
 // column tables of the table walker: entries per view and column (nx + ny - 1 + padding), total, build
 int coltab_kmax(const KGeom &kg);
 size_t coltab_entries(const KGeom &kg, int n_views_total);
+long long brick_slice(int nx, int ny);  // elements of one bricked z slice
+size_t brick_bytes(const KGeom &kg);    // the bricked copy of the N_p phases at 4 bytes per voxel
 tnlm_status build_coltab(const KGeom &kg, const ViewGeom *views, int n_views_total, float2 *tab, cudaStream_t st);
 
 // vout = beta * vin + alpha * P^T proj.  scaled: proj already multiplied by
@@ -258,6 +266,7 @@ struct tnlm_geometry {
     double *d_scalars = nullptr;      // reduction results
     float *d_pref = nullptr;          // column prefix sums for the transpose (prefix_floats)
     float2 *d_coltab = nullptr;       // column tables of the table projector (coltab_entries)
+    void *d_volb = nullptr;           // its bricked volume copy (brick_bytes)
     bool coltab_failed = false;       // their allocation failed once: the slab walker runs
     // CGLS workspace (allocated on first use)
     float *d_q = nullptr;             // sum(n_views) * npix
@@ -280,9 +289,10 @@ namespace tnlm {
 // the band-transpose prefix array (nullptr when the geometry does not admit
 // that transpose or the allocation failed).
 tnlm_status ensure_workspace(tnlm_geometry *g, bool need_tmp, long long n_scalars);
-// Column tables of the table projector: built on first use (synchronising the
-// device, so never during stream capture); on allocation failure the slab
-// walker runs instead (the same model, FP32 rounding of its own).
+// Column tables of the table projector and its bricked volume copy: built and
+// allocated on first use (synchronising the device, so never during stream
+// capture); on allocation failure the slab walker runs instead (the same
+// model, FP32 rounding of its own).
 void ensure_coltab(tnlm_geometry *g);
 float *prefix_workspace(tnlm_geometry *g);
 }  // namespace tnlm

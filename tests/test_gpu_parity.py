@@ -1007,6 +1007,7 @@ def test_out_of_memory_paths_and_recovery(ora):
     assert lib.tnlm_test_fail_allocations(1) == 0
     px = tnlm.tnlm_project(G4, cuda(x)).cpu().numpy()
     assert lib.tnlm_test_fail_allocations(0) == 0
+    assert tnlm.tnlm_get_launch_shapes(G4)["projector_rows"] == 4
     assert rel_l2(px, ora.project(ora.Geometry(GEOMS["ragged_uneven"]), x)) <= RTOL
     G4.close()
     g = cuda(synth.smooth_volume((3, 8, 12, 16), 5))

@@ -27,6 +27,10 @@ def test_projector_and_transpose_shapes_bitwise_equal(name):
     G = tnlm.Geometry(GEOMS[name])
     x = cuda(synth.uniform(G.vol_shape, 300))
     r = cuda(synth.uniform(G.proj_shape, 301))
+    # a new handle starts at the table shape 104 and runs the slab walker until its tables exist
+    assert tnlm.tnlm_get_launch_shapes(G)["projector_rows"] == 4
+    tnlm.tnlm_project(G, x)
+    assert tnlm.tnlm_get_launch_shapes(G)["projector_rows"] == 104
     outs_p, outs_b = [], []
     outs_t = []
     for rows in (2, 4, 8):  # the slab walker
@@ -34,6 +38,7 @@ def test_projector_and_transpose_shapes_bitwise_equal(name):
         outs_p.append(tnlm.tnlm_project(G, x))
     for rows in (102, 104, 108):  # the table walker
         tnlm.tnlm_set_launch_shapes(G, rows, 8, 4)
+        assert tnlm.tnlm_get_launch_shapes(G) == {"projector_rows": rows, "transpose_cells": 8, "transpose_rows": 4}
         outs_t.append(tnlm.tnlm_project(G, x))
     for cells in (4, 8):
         for rows in (2, 4):
