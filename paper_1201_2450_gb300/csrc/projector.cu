@@ -369,12 +369,15 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             float bcur = blo;
             const float2 *__restrict__ tp = tc + k0 * st;
             float2 t0 = __ldg(tp), t1 = __ldg(tp + st);
-            for (int k = k0; k <= k1; k += 2) {
+            // entries before k1 end before bhi (the tables ascend), so only the last entry is clamped
+            // to the row's exit: pairs of entries strictly before k1 first, then the last one or two
+            int k = k0;
+            for (; k + 1 < k1; k += 2) {
                 tp += 2 * st;
-                const float2 n0 = __ldg(tp), n1 = __ldg(tp + st);  // entries k+2, k+3 (padding past the exit)
+                const float2 n0 = __ldg(tp), n1 = __ldg(tp + st);  // entries k+2, k+3 (at most k1 + 1)
                 float f0 = ldg_v(fp + __float_as_int(t0.y));
                 float f1 = ldg_v(fp + __float_as_int(t1.y));
-                float e = fminf(t0.x, bhi);
+                float e = t0.x;
                 if (bc < e) {
                     do {  // z crossings inside entry k's segment
                         acc = fmaf(f0, bc - bcur, acc);
@@ -388,21 +391,34 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                 }
                 acc = fmaf(f0, e - bcur, acc);
                 bcur = e;
-                if (k < k1) {
-                    e = fminf(t1.x, bhi);
-                    while (bc < e) {  // z crossings inside entry k+1's segment
-                        acc = fmaf(f1, bc - bcur, acc);
-                        bcur = bc;
-                        fp += zstep;
-                        f1 = ldg_v(fp + __float_as_int(t1.y));
-                        fc += scf;
-                        bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
-                    }
-                    acc = fmaf(f1, e - bcur, acc);
-                    bcur = e;
+                e = t1.x;
+                while (bc < e) {  // z crossings inside entry k+1's segment
+                    acc = fmaf(f1, bc - bcur, acc);
+                    bcur = bc;
+                    fp += zstep;
+                    f1 = ldg_v(fp + __float_as_int(t1.y));
+                    fc += scf;
+                    bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
                 }
+                acc = fmaf(f1, e - bcur, acc);
+                bcur = e;
                 t0 = n0;
                 t1 = n1;
+            }
+            for (; k <= k1; ++k) {  // entries k1 - 1 (if not taken above) and k1
+                float f0 = ldg_v(fp + __float_as_int(t0.y));
+                const float e = fminf(t0.x, bhi);
+                while (bc < e) {
+                    acc = fmaf(f0, bc - bcur, acc);
+                    bcur = bc;
+                    fp += zstep;
+                    f0 = ldg_v(fp + __float_as_int(t0.y));
+                    fc += scf;
+                    bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
+                }
+                acc = fmaf(f0, e - bcur, acc);
+                bcur = e;
+                t0 = t1;
             }
         }
         const float pf = acc * len;

@@ -13,13 +13,17 @@
 
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "tnlm_internal.cuh"
 
 namespace tnlm {
 namespace box {
 
-constexpr float kRescale = 16.f;  // lazy-rescale threshold (log2 units), as in the direct sweep
+// lazy-rescale threshold (log2 units): a running reference moves only when a
+// candidate's weight exceeds it by 2^kRescale, so every weight and sum stays
+// below 2^kRescale times the candidate count and the normaliser Z >= 1
+constexpr float kRescale = 64.f;
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -124,6 +128,16 @@ __device__ __forceinline__ float2 xbox2(float2 b)
 // One direction of the sweep for this thread's 2 x BZ outputs (y rows j = 0, 1
 // are processed as FP32x2 pairs).  ai holds the thread's patch block of phase
 // i as [z][y pair]; res accumulates N/Z per output.
+// The window offsets are taken column by column, (dy, dx) = (0, 0) first and
+// then the others in row-major order, dz ascending within a column.  The
+// running reference of the online normalisation (mref = c2 D of the reference
+// candidate, log2 units) moves only when a candidate beats it by more than
+// 2^kRescale.  A candidate's log2 weight against the reference is
+// a = mref - c2 D <= mref (D >= 0), so once every output of a warp has
+// mref <= kRescale no later candidate can move it: after the first column the
+// warp votes, and interior tiles whose warp passed skip the test for the
+// remaining columns (the same operations on every output otherwise, so the
+// result does not depend on the vote).
 // STORE: also write every patch distance of the thread's outputs to Gd[delta][voxel] (delta-major, delta =
 // ((dz + M) S + dy + M) S + dx + M), for the phase-pair form of the sweep (k_pair_b reads them back).
 template <int D_, int M_, int BZ, int WY_, int WZ_, bool INTERIOR, bool STORE = false>
@@ -135,6 +149,7 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
     constexpr int BY = 2;
     using C = BoxCfg<D_, M_, BY, BZ, WY_, WZ_>;
     constexpr int SP = C::SY / 2;  // y pairs of the patch block
+    constexpr int S = 2 * M_ + 1;
     float2 mref[BZ], N[BZ], Z[BZ];
 #pragma unroll
     for (int k = 0; k < BZ; ++k) {
@@ -143,107 +158,126 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
         Z[k] = make_float2(0.f, 0.f);
     }
     const float2 nc2 = make_float2(-c2, -c2);
-    for (int dy = -M_; dy <= M_; ++dy) {
+    // the candidates of window column (dy, dx), dz = -M .. M
+    auto column = [&](int dy, int dx, auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
         const bool vy0 = INTERIOR || (unsigned)(yb + dy) < (unsigned)ny;
         const bool vy1 = INTERIOR || (unsigned)(yb + 1 + dy) < (unsigned)ny;
-        for (int dx = -M_; dx <= M_; ++dx) {
-            const bool vx = INTERIOR || (unsigned)(x + dx) < (unsigned)nx;
-            const bool vxy0 = vx && vy0, vxy1 = vx && vy1;
-            const float *paj = s_aj + (wy * BY + dy + M_) * C::AJX + lane + dx + M_;
-            const float *pvj = s_vj + (wy * BY + dy + M_) * C::VJX + lane + dx + M_;
-            // neighbour-phase rows along z, a sliding window of SZ rows of y pairs
-            float2 aw[2 * M_ + C::SZ][SP];
-            float2 vw[2 * M_ + BZ];
+        const bool vx = INTERIOR || (unsigned)(x + dx) < (unsigned)nx;
+        const bool vxy0 = vx && vy0, vxy1 = vx && vy1;
+        const float *paj = s_aj + (wy * BY + dy + M_) * C::AJX + lane + dx + M_;
+        const float *pvj = s_vj + (wy * BY + dy + M_) * C::VJX + lane + dx + M_;
+        // neighbour-phase rows along z, a sliding window of SZ rows of y pairs
+        float2 aw[2 * M_ + C::SZ][SP];
+        float2 vw[2 * M_ + BZ];
 #pragma unroll
-            for (int r = 0; r < C::SZ - 1; ++r)
+        for (int r = 0; r < C::SZ - 1; ++r)
+#pragma unroll
+            for (int p = 0; p < SP; ++p) {
+                const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
+                aw[r][p] = make_float2(q0[0], q0[C::AJX]);
+            }
+#pragma unroll
+        for (int r = 0; r < BZ - 1; ++r) {
+            const float *q0 = pvj + (wz * BZ + r) * C::VJY * C::VJX;
+            vw[r] = make_float2(q0[0], q0[C::VJX]);
+        }
+#pragma unroll
+        for (int q = 0; q <= 2 * M_; ++q) {  // q = dz + M
+            {
+                const int r = q + C::SZ - 1;
 #pragma unroll
                 for (int p = 0; p < SP; ++p) {
                     const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
                     aw[r][p] = make_float2(q0[0], q0[C::AJX]);
                 }
-#pragma unroll
-            for (int r = 0; r < BZ - 1; ++r) {
-                const float *q0 = pvj + (wz * BZ + r) * C::VJY * C::VJX;
-                vw[r] = make_float2(q0[0], q0[C::VJX]);
+                const int rv = q + BZ - 1;
+                const float *q1 = pvj + (wz * BZ + rv) * C::VJY * C::VJX;
+                vw[rv] = make_float2(q1[0], q1[C::VJX]);
             }
+            // squared differences and z box sums, per y pair
+            float2 bz[BZ][SP];
 #pragma unroll
-            for (int q = 0; q <= 2 * M_; ++q) {  // q = dz + M
-                {
-                    const int r = q + C::SZ - 1;
+            for (int p = 0; p < SP; ++p) {
+                float2 sq[C::SZ];
 #pragma unroll
-                    for (int p = 0; p < SP; ++p) {
-                        const float *q0 = paj + ((wz * BZ + r) * C::AJY + 2 * p) * C::AJX;
-                        aw[r][p] = make_float2(q0[0], q0[C::AJX]);
-                    }
-                    const int rv = q + BZ - 1;
-                    const float *q1 = pvj + (wz * BZ + rv) * C::VJY * C::VJX;
-                    vw[rv] = make_float2(q1[0], q1[C::VJX]);
-                }
-                // squared differences and z box sums, per y pair
-                float2 bz[BZ][SP];
-#pragma unroll
-                for (int p = 0; p < SP; ++p) {
-                    float2 sq[C::SZ];
-#pragma unroll
-                    for (int zz = 0; zz < C::SZ; ++zz) {
-                        const float2 t = __fadd2_rn(ai[zz][p], make_float2(-aw[q + zz][p].x, -aw[q + zz][p].y));
-                        sq[zz] = __fmul2_rn(t, t);
-                    }
-#pragma unroll
-                    for (int k = 0; k < BZ; ++k) {
-                        float2 acc = sq[k];
-#pragma unroll
-                        for (int t = 1; t <= 2 * D_; ++t) acc = __fadd2_rn(acc, sq[k + t]);
-                        bz[k][p] = acc;
-                    }
+                for (int zz = 0; zz < C::SZ; ++zz) {
+                    const float2 t = __fadd2_rn(ai[zz][p], make_float2(-aw[q + zz][p].x, -aw[q + zz][p].y));
+                    sq[zz] = __fmul2_rn(t, t);
                 }
 #pragma unroll
                 for (int k = 0; k < BZ; ++k) {
-                    // y box sums of the two output rows: row 0 sums y 0..2d, row 1 sums y 1..2d+1,
-                    // both direct sums sharing the middle rows m = y 1..2d
-                    float m = bz[k][0].y;
+                    float2 acc = sq[k];
 #pragma unroll
-                    for (int yy = 2; yy <= 2 * D_; ++yy) m += (yy & 1) ? bz[k][yy / 2].y : bz[k][yy / 2].x;
-                    const float2 yb2 = make_float2(bz[k][0].x + m, m + bz[k][SP - 1].y);
-                    const float2 Dv = xbox2<D_>(yb2);  // patch distances of outputs (0,k) and (1,k)
-                    if constexpr (STORE) {
-                        constexpr int S = 2 * M_ + 1;
-                        const long long nvox = (long long)nx * ny * nz;
-                        const int z = zb + k;
-                        if (z < nz) {
-                            float *gp = Gd + (long long)((q * S + dy + M_) * S + dx + M_) * nvox +
-                                        ((long long)z * ny + yb) * nx + x;
-                            if (st0) gp[0] = Dv.x;
-                            if (st1) gp[nx] = Dv.y;
-                        }
-                    }
-                    float2 a = __ffma2_rn(Dv, nc2, mref[k]);  // log2 weights vs the references
-                    const bool vz = INTERIOR || (unsigned)(zb + k + q - M_) < (unsigned)nz;
-                    if (!INTERIOR) {
-                        if (!(vxy0 && vz)) a.x = -FLT_MAX;
-                        if (!(vxy1 && vz)) a.y = -FLT_MAX;
-                    }
-                    if (fmaxf(a.x, a.y) > kRescale) {  // rare: one test for both outputs of the pair
-                        if (a.x > kRescale) {  // candidate beats the reference by 2^kRescale: move it
-                            const float sc = ex2(-a.x);
-                            N[k].x *= sc;
-                            Z[k].x *= sc;
-                            mref[k].x = Dv.x * c2;
-                            a.x = 0.f;
-                        }
-                        if (a.y > kRescale) {
-                            const float sc = ex2(-a.y);
-                            N[k].y *= sc;
-                            Z[k].y *= sc;
-                            mref[k].y = Dv.y * c2;
-                            a.y = 0.f;
-                        }
-                    }
-                    const float2 e = make_float2(ex2(a.x), ex2(a.y));
-                    N[k] = __ffma2_rn(e, vw[q + k], N[k]);
-                    Z[k] = __fadd2_rn(Z[k], e);
+                    for (int t = 1; t <= 2 * D_; ++t) acc = __fadd2_rn(acc, sq[k + t]);
+                    bz[k][p] = acc;
                 }
             }
+#pragma unroll
+            for (int k = 0; k < BZ; ++k) {
+                // y box sums of the two output rows: row 0 sums y 0..2d, row 1 sums y 1..2d+1,
+                // both direct sums sharing the middle rows m = y 1..2d
+                float m = bz[k][0].y;
+#pragma unroll
+                for (int yy = 2; yy <= 2 * D_; ++yy) m += (yy & 1) ? bz[k][yy / 2].y : bz[k][yy / 2].x;
+                const float2 yb2 = make_float2(bz[k][0].x + m, m + bz[k][SP - 1].y);
+                const float2 Dv = xbox2<D_>(yb2);  // patch distances of outputs (0,k) and (1,k)
+                if constexpr (STORE) {
+                    const long long nvox = (long long)nx * ny * nz;
+                    const int z = zb + k;
+                    if (z < nz) {
+                        float *gp = Gd + (long long)((q * S + dy + M_) * S + dx + M_) * nvox +
+                                    ((long long)z * ny + yb) * nx + x;
+                        if (st0) gp[0] = Dv.x;
+                        if (st1) gp[nx] = Dv.y;
+                    }
+                }
+                float2 a = __ffma2_rn(Dv, nc2, mref[k]);  // log2 weights vs the references
+                const bool vz = INTERIOR || (unsigned)(zb + k + q - M_) < (unsigned)nz;
+                if (!INTERIOR) {
+                    if (!(vxy0 && vz)) a.x = -FLT_MAX;
+                    if (!(vxy1 && vz)) a.y = -FLT_MAX;
+                }
+                if (CHECK && fmaxf(a.x, a.y) > kRescale) {  // rare: one test for both outputs of the pair
+                    if (a.x > kRescale) {  // candidate beats the reference by 2^kRescale: move it
+                        const float sc = ex2(-a.x);
+                        N[k].x *= sc;
+                        Z[k].x *= sc;
+                        mref[k].x = Dv.x * c2;
+                        a.x = 0.f;
+                    }
+                    if (a.y > kRescale) {
+                        const float sc = ex2(-a.y);
+                        N[k].y *= sc;
+                        Z[k].y *= sc;
+                        mref[k].y = Dv.y * c2;
+                        a.y = 0.f;
+                    }
+                }
+                const float2 e = make_float2(ex2(a.x), ex2(a.y));
+                N[k] = __ffma2_rn(e, vw[q + k], N[k]);
+                Z[k] = __fadd2_rn(Z[k], e);
+            }
+        }
+    };
+    constexpr int kCentre = M_ * S + M_;
+    bool settled = false;  // every output of the warp has mref <= kRescale (interior tiles only)
+    for (int it = 0; it < S * S; ++it) {
+        const int c = it == 0 ? kCentre : (it - 1 < kCentre ? it - 1 : it);
+        const int dy = c / S - M_, dx = c % S - M_;
+        if (INTERIOR && settled)
+            column(dy, dx, std::false_type{});
+        else
+            column(dy, dx, std::true_type{});
+        if (INTERIOR && it == 0) {
+            // outputs of this thread: lanes d .. 31 - d (the others are the x halo); interior
+            // tiles hold no row or slice outside the volume
+            bool ok = true;
+            if (lane >= D_ && lane < 32 - D_) {
+#pragma unroll
+                for (int k = 0; k < BZ; ++k) ok = ok && mref[k].x <= kRescale && mref[k].y <= kRescale;
+            }
+            settled = __all_sync(0xffffffffu, ok);
         }
     }
 #pragma unroll

@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(BoxCfg<D_, M_, BY, BZ, WY_, WZ_>::NT)
     }
 }
 
-// Pass B: output y of phase i toward phase i-1 from the distances of pair (i-1, i), in the order and
-// with the online normalisation of box_direction; adds N/Z to the partial result, then Eq. 8.
+// Pass B: output y of phase i toward phase i-1 from the distances of pair (i-1, i), in the candidate
+// order and with the online normalisation of box_direction; adds N/Z to the partial result, then Eq. 8.
 template <int M_>
 __global__ void __launch_bounds__(256)
     k_pair_b(int nx, int ny, int nz, const float *__restrict__ G, const float *__restrict__ vprev,
@@ -97,28 +97,28 @@ __global__ void __launch_bounds__(256)
     if (t >= nvox) return;
     const int x = (int)(t % nx), y = (int)((t / nx) % ny), z = (int)(t / ((long long)nx * ny));
     float mref = FLT_MAX, N = 0.f, Z = 0.f;
-    for (int dy = -M_; dy <= M_; ++dy) {
-        if ((unsigned)(y + dy) >= (unsigned)ny) continue;
-        for (int dx = -M_; dx <= M_; ++dx) {
-            if ((unsigned)(x + dx) >= (unsigned)nx) continue;
+    constexpr int kCentre = M_ * S + M_;
+    for (int it = 0; it < S * S; ++it) {  // window columns (dy, dx): (0, 0) first, then row-major
+        const int cc = it == 0 ? kCentre : (it - 1 < kCentre ? it - 1 : it);
+        const int dy = cc / S - M_, dx = cc % S - M_;
+        if ((unsigned)(y + dy) >= (unsigned)ny || (unsigned)(x + dx) >= (unsigned)nx) continue;
 #pragma unroll
-            for (int dz = -M_; dz <= M_; ++dz) {
-                if ((unsigned)(z + dz) >= (unsigned)nz) continue;
-                const long long c = ((long long)(z + dz) * ny + (y + dy)) * nx + (x + dx);  // candidate in phase i-1
-                // its pair distance, stored by pass A at offset -delta
-                const float D = __ldg(G + (long long)(((M_ - dz) * S + (M_ - dy)) * S + (M_ - dx)) * nvox + c);
-                float a = fmaf(D, -c2, mref);
-                if (a > kRescale) {
-                    const float sc = ex2(-a);
-                    N *= sc;
-                    Z *= sc;
-                    mref = D * c2;
-                    a = 0.f;
-                }
-                const float e = ex2(a);
-                N = fmaf(e, __ldg(vprev + c), N);
-                Z += e;
+        for (int dz = -M_; dz <= M_; ++dz) {
+            if ((unsigned)(z + dz) >= (unsigned)nz) continue;
+            const long long c = ((long long)(z + dz) * ny + (y + dy)) * nx + (x + dx);  // candidate in phase i-1
+            // its pair distance, stored by pass A at offset -delta
+            const float D = __ldg(G + (long long)(((M_ - dz) * S + (M_ - dy)) * S + (M_ - dx)) * nvox + c);
+            float a = fmaf(D, -c2, mref);
+            if (a > kRescale) {
+                const float sc = ex2(-a);
+                N *= sc;
+                Z *= sc;
+                mref = D * c2;
+                a = 0.f;
             }
+            const float e = ex2(a);
+            N = fmaf(e, __ldg(vprev + c), N);
+            Z += e;
         }
     }
     const float r = out[t] + N / Z;
