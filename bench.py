@@ -48,11 +48,11 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 NCU_TRAFFIC = {
     # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload; the
     # projector stage is the bricked copy plus the table walk, the transpose stage the column scan plus the bands
-    "k_forward": {"bytes_per_launch": int((100.747008e6 + 48.406272e6 + 595.252736e6 + 162.568448e6) * 10 / 6),
-                  "source_sha": "b253635451a9a7ba"},
+    "k_forward": {"bytes_per_launch": int((100.750848e6 + 48.628480e6 + 592.987392e6 + 162.353920e6) * 10 / 6),
+                  "source_sha": "4d2e1dace0dc409b"},
     "k_backproject": {"bytes_per_launch": int((169.893632e6 + 284.609024e6 + 558.020096e6 + 93.149184e6) * 10 / 6),
                       "source_sha": "35125fe705d5a4a4"},
-    "k_sweep": {"bytes_per_launch": int((160.676608e6 + 84.272896e6) * 10 / 6), "source_sha": "5c1e717465e6a4bc"},
+    "k_sweep": {"bytes_per_launch": int((162.544640e6 + 83.844608e6) * 10 / 6), "source_sha": "aa475743b3412a05"},
 }
 
 

@@ -135,9 +135,9 @@ __device__ __forceinline__ float2 xbox2(float2 b)
 // 2^kRescale.  A candidate's log2 weight against the reference is
 // a = mref - c2 D <= mref (D >= 0), so once every output of a warp has
 // mref <= kRescale no later candidate can move it: after the first column the
-// warp votes, and interior tiles whose warp passed skip the test for the
-// remaining columns (the same operations on every output otherwise, so the
-// result does not depend on the vote).
+// warp votes, and a warp that passed skips the test for the remaining
+// columns (the same operations on every output otherwise, so the result does
+// not depend on the vote).
 // STORE: also write every patch distance of the thread's outputs to Gd[delta][voxel] (delta-major, delta =
 // ((dz + M) S + dy + M) S + dx + M), for the phase-pair form of the sweep (k_pair_b reads them back).
 template <int D_, int M_, int BZ, int WY_, int WZ_, bool INTERIOR, bool STORE = false>
@@ -261,21 +261,25 @@ __device__ __forceinline__ void box_direction(const float2 (&ai)[BZ + 2 * D_][(2
         }
     };
     constexpr int kCentre = M_ * S + M_;
-    bool settled = false;  // every output of the warp has mref <= kRescale (interior tiles only)
+    bool settled = false;  // every output of the warp has mref <= kRescale
     for (int it = 0; it < S * S; ++it) {
         const int c = it == 0 ? kCentre : (it - 1 < kCentre ? it - 1 : it);
         const int dy = c / S - M_, dx = c % S - M_;
-        if (INTERIOR && settled)
+        if (settled)
             column(dy, dx, std::false_type{});
         else
             column(dy, dx, std::true_type{});
-        if (INTERIOR && it == 0) {
-            // outputs of this thread: lanes d .. 31 - d (the others are the x halo); interior
-            // tiles hold no row or slice outside the volume
+        if (it == 0) {
+            // this thread's outputs inside the volume (lanes d .. 31 - d; the others are the x
+            // halo): the centre column holds the output itself, so each has a reference by now
             bool ok = true;
-            if (lane >= D_ && lane < 32 - D_) {
+            if (lane >= D_ && lane < 32 - D_ && x < nx) {
 #pragma unroll
-                for (int k = 0; k < BZ; ++k) ok = ok && mref[k].x <= kRescale && mref[k].y <= kRescale;
+                for (int k = 0; k < BZ; ++k) {
+                    if (zb + k < nz) {
+                        ok = ok && (yb >= ny || mref[k].x <= kRescale) && (yb + 1 >= ny || mref[k].y <= kRescale);
+                    }
+                }
             }
             settled = __all_sync(0xffffffffu, ok);
         }
