@@ -50,8 +50,8 @@ NCU_TRAFFIC = {
     # projector stage is the bricked copy plus the table walk, the transpose stage the column scan plus the bands
     "k_forward": {"bytes_per_launch": int((100.750848e6 + 48.628480e6 + 592.987392e6 + 162.353920e6) * 10 / 6),
                   "source_sha": "4d2e1dace0dc409b"},
-    "k_backproject": {"bytes_per_launch": int((169.893632e6 + 284.609024e6 + 558.020096e6 + 93.149184e6) * 10 / 6),
-                      "source_sha": "35125fe705d5a4a4"},
+    "k_backproject": {"bytes_per_launch": int((169.919488e6 + 284.322560e6 + 556.931328e6 + 93.128448e6) * 10 / 6),
+                      "source_sha": "5aa935fcb93c583b"},
     "k_sweep": {"bytes_per_launch": int((162.544640e6 + 83.844608e6) * 10 / 6), "source_sha": "aa475743b3412a05"},
 }
 

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_colscan(KGeom G, const float *__restric
 //
 // One view of a thread's column chunk: every pixel column iu of the column's
 // footprint, each of its chord's cell boundaries in turn.
-template <bool SCALED, int CH>
+template <int CH>
 __device__ __forceinline__ void bands_view(const KGeom &G, const float4 *s_row, float c, float s, float xc, float yc,
                                            int iz0, int nzc, float fvscale, float fvoff,
                                            const float *__restrict__ pv, const float2 *__restrict__ ppv,
@@ -237,7 +237,7 @@ __device__ __forceinline__ void bands_view(const KGeom &G, const float4 *s_row, 
         if (!ok || !(glo < ghi)) continue;
         const float dg = ghi - glo;  // xy chord of this pixel column (ray-parameter units)
         const float sra = __fdividef(fvscale, ac + glo), srb = __fdividef(fvscale, ac + ghi);  // row maps (margin)
-        const float len_u2 = G.sdd * G.sdd + u * u;
+        const float gmid = 0.5f * (glo + ghi);  // the chord's midpoint
         const float *__restrict__ pc = pv + iu;
         const float2 *__restrict__ pp = ppv + iu;
         // first and last detector row of boundary zm's band (1e-3-row margins); the integer
@@ -269,18 +269,16 @@ __device__ __forceinline__ void bands_view(const KGeom &G, const float4 *s_row, 
             const int r0 = max(0, blo_m), r1 = min(G.nv - 1, bhi_m);
             float rband = 0.f;  // sum of the band rows' values
             auto band_row = [&](int iv, bool on) {
-                const float4 rw = s_row[iv];
+                const float4 rw = s_row[iv];  // (v, 1/|v|, sign of v)
                 float r = __ldg(pc + iv * G.nu);
-                if (!SCALED) r *= sqrtf(len_u2 + rw.z);
                 r = on ? r : 0.f;  // a row outside the band adds nothing
                 rband += r;
-                float below;  // part of the chord below z = zm
-                if (rw.x != 0.f) {
-                    const float gs = fmaf(-ac, rw.x, zm) * rw.y;  // crossing parameter (column-relative)
-                    below = rw.x > 0.f ? fminf(fmaxf(gs - glo, 0.f), dg) : fminf(fmaxf(ghi - gs, 0.f), dg);
-                } else {
-                    below = zm > 0.f ? dg : 0.f;  // ray in the plane z = 0 (half-open cells)
-                }
+                // part of the chord below z = zm: the ray rises (v > 0) or falls (v < 0) through the
+                // crossing gs = (zm - ac v) / v, so below = clamp(sign(v) (gs - gmid) + dg / 2, 0, dg);
+                // a ray in the plane z = 0 (v = 0, 1/|v| = inf) lies below every zm > 0 and above
+                // every zm <= 0 (half-open cells): +-inf, or NaN for zm = 0, clamp to dg and 0
+                const float sgs = fmaf(-ac, rw.x, zm) * rw.y;  // sign(v) * gs
+                const float below = fminf(fmaxf(fmaf(0.5f, dg, fmaf(-rw.z, gmid, sgs)), 0.f), dg);
                 if (m > 0) acc[m - 1] = fmaf(r, below, acc[m - 1]);
                 if (m < nzc) acc[m] = fmaf(r, dg - below, acc[m]);
             };
@@ -299,19 +297,22 @@ __device__ __forceinline__ void bands_view(const KGeom &G, const float4 *s_row, 
     }
 }
 
-template <bool SCALED, int CH, int BY, class T>
-__global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
+// Launch bounds: 36 warps per SM (9 blocks of 32 x 4 threads, 18 of 32 x 2), 56 registers per thread; at
+// 48 registers the band-row split spills.  The input is the ray-length-scaled residual (k_colscan writes a
+// scaled copy of an unscaled input).
+template <int CH, int BY, class T>
+__global__ void __launch_bounds__(kBpBX *BY, 36 / BY)
     k_backproject_bands(KGeom G, const ViewGeom *__restrict__ views, const int *__restrict__ view_off,
                         const float *__restrict__ proj, const float2 *__restrict__ pref, const T *vin,
                         T *vout, float alpha, float beta, int nchunks)
 {
     constexpr int NT = kBpBX * BY;
     extern __shared__ float4 sm4[];
-    float4 *s_row = sm4;  // per detector row: (v, 1/v or 0, v^2, 0)
+    float4 *s_row = sm4;  // per detector row: (v, 1/|v| or +inf, sign of v (+1 for v = 0), 0)
     const int tid = threadIdx.y * kBpBX + threadIdx.x;
     for (int t = tid; t < G.nv; t += NT) {
         const float v = ((float)t - G.vc) * G.dv + G.v_off;
-        s_row[t] = make_float4(v, v != 0.f ? 1.0f / v : 0.f, v * v, 0.f);
+        s_row[t] = make_float4(v, v != 0.f ? 1.0f / fabsf(v) : INFINITY, v < 0.f ? -1.f : 1.f, 0.f);
     }
     __syncthreads();
     const int ix = blockIdx.x * kBpBX + threadIdx.x;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(kBpBX *BY, 40 / BY)
         const float c = views[vg].c, s = views[vg].s;
         const float *__restrict__ pv = proj + (long long)vg * G.npix;
         const float2 *__restrict__ ppv = pref + (long long)vg * (G.nv + 1) * G.nu;
-        bands_view<SCALED, CH>(G, s_row, c, s, xc, yc, iz0, nzc, fvscale, fvoff, pv, ppv, acc);
+        bands_view<CH>(G, s_row, c, s, xc, yc, iz0, nzc, fvscale, fvoff, pv, ppv, acc);
     }
     const long long base = (long long)phase * G.nvox + ((long long)iz0 * G.ny + iy) * G.nx + ix;
 #pragma unroll
@@ -370,9 +371,9 @@ static tnlm_status launch_bands(const KGeom &kg, const ViewGeom *views, const in
     dim3 grid((kg.nx + kBpBX - 1) / kBpBX, (kg.ny + BY - 1) / BY, kg.np * nchb);
     const size_t smem = sizeof(float4) * kg.nv;
     if (smem > 48 * 1024)
-        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<true, CH, BY, T>,
+        TNLM_TRY_CUDA(cudaFuncSetAttribute(k_backproject_bands<CH, BY, T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_backproject_bands<true, CH, BY, T><<<grid, dim3(kBpBX, BY), smem, st>>>(kg, views, view_off, src, pref, vin, vout,
+    k_backproject_bands<CH, BY, T><<<grid, dim3(kBpBX, BY), smem, st>>>(kg, views, view_off, src, pref, vin, vout,
                                                                                alpha, beta, nchb);
     TNLM_TRY_CUDA(cudaGetLastError());
     return TNLM_OK;
