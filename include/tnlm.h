@@ -194,6 +194,24 @@ tnlm_status tnlm_p1(tnlm_geometry *geom, const float *y, const float *f, float *
 tnlm_status tnlm_reconstruct(tnlm_geometry *geom, const float *y, float *f, const tnlm_params *params,
                              double *report, void *stream);
 
+/* tnlm_reconstruct from and to HOST buffers, with the copies inside the call:
+ * y_host [sum n_views][nv][nu] and f_host [N_p][nz][ny][nx] (f^(0) on entry,
+ * f^(n_outer) once `stream` has completed) are copied to the caller's device
+ * buffers y_dev and f_dev (same shapes, overwritten), the run is enqueued on
+ * `stream`, and f_dev is copied back to f_host.  The host-to-device copies go
+ * phase by phase on a stream of the handle, after the work already queued on
+ * `stream`; with gradient steps (p1_solver = 0) the first projection of each
+ * phase starts as soon as that phase has arrived, so the copies of the later
+ * phases overlap the projection of the earlier ones (page-locked host memory
+ * is needed for the overlap).  The result equals tnlm_reconstruct on the
+ * copied inputs bit for bit.  The call returns when everything is enqueued
+ * (when report is given it synchronises `stream`, as tnlm_reconstruct): read
+ * f_host after synchronising `stream`.  The first call creates the handle's
+ * copy stream and one event per phase.  TNLM_ERR_ARG for a NULL pointer or as
+ * tnlm_reconstruct. */
+tnlm_status tnlm_reconstruct_host(tnlm_geometry *geom, const float *y_host, float *f_host, float *y_dev, float *f_dev,
+                                  const tnlm_params *params, double *report, void *stream);
+
 /* TNLM-R with BF16 storage and FP32 arithmetic: y ([sum n_views][nv][nu])
  * and f ([N_p][nz][ny][nx]) are bfloat16 bit patterns, and so are the
  * handle's g^(k) image and sweep scratch (in its FP32-sized workspace).

@@ -116,6 +116,7 @@ def _load():
             "tnlm_set_batch_sweep_mode": (i, [i]),
             "tnlm_p1": (i, [vp, vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_reconstruct": (i, [vp, vp, vp, C.POINTER(_Params), vp, vp]),
+            "tnlm_reconstruct_host": (i, [vp, vp, vp, vp, vp, C.POINTER(_Params), vp, vp]),
             "tnlm_enhance": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_enhance_noalloc": (i, [i, i, i, i, vp, vp, C.POINTER(_Params), vp]),
             "tnlm_operator_norm": (i, [vp, vp, i, C.POINTER(C.c_double), vp]),
@@ -658,17 +659,37 @@ def tnlm_operator_norm(geom: Geometry, x: torch.Tensor, n_iter: int = 30, stream
     return L.value
 
 
+def _host(t: torch.Tensor, name: str, shape) -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be torch.float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
 def reconstruct_host(geom: Geometry, y_host: torch.Tensor, f_host: torch.Tensor, params: Params,
-                     y_dev: torch.Tensor | None = None, f_dev: torch.Tensor | None = None, stream=None):
-    """TNLM-R on host (pinned) buffers: copy y and f to the device, run
-    tnlm_reconstruct, copy f back into f_host.  Returns the H2D and D2H byte
-    counts."""
+                     y_dev: torch.Tensor | None = None, f_dev: torch.Tensor | None = None, stream=None,
+                     report: bool = False):
+    """TNLM-R on host buffers through tnlm_reconstruct_host: the copies to
+    y_dev / f_dev, the run and the copy of f back into f_host, enqueued on the
+    stream (pinned host memory lets the copies overlap the first projection).
+    f_host holds the result once the stream has completed.  Returns the H2D
+    and D2H byte counts (and the report when asked)."""
     if y_dev is None:
         y_dev = torch.empty(geom.proj_shape, dtype=torch.float32, device=geom.device)
     if f_dev is None:
         f_dev = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
-    y_dev.copy_(y_host, non_blocking=True)
-    f_dev.copy_(f_host, non_blocking=True)
-    tnlm_reconstruct(geom, y_dev, f_dev, params, stream=stream)
-    f_host.copy_(f_dev, non_blocking=True)
-    return y_host.numel() * 4 + f_host.numel() * 4, f_host.numel() * 4
+    rep = np.zeros((params.n_outer, params.n_inner), np.float64) if report else None
+    p = params._c()
+    _check(_load().tnlm_reconstruct_host(geom.handle, _host(y_host, "y_host", geom.proj_shape),
+                                         _host(f_host, "f_host", geom.vol_shape),
+                                         _dev(y_dev, "y_dev", geom.device, geom.proj_shape),
+                                         _dev(f_dev, "f_dev", geom.device, geom.vol_shape), C.byref(p),
+                                         rep.ctypes.data if rep is not None else None, _stream(stream)),
+           "tnlm_reconstruct_host")
+    counts = (y_host.numel() * 4 + f_host.numel() * 4, f_host.numel() * 4)
+    return counts + (rep,) if report else counts

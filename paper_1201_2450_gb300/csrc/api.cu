@@ -355,6 +355,9 @@ void tnlm_destroy_geometry(tnlm_geometry *g)
     cudaFree(g->d_pref);
     cudaFree(g->d_coltab);
     cudaFree(g->d_volb);
+    for (cudaEvent_t e : g->phase_ready) cudaEventDestroy(e);
+    if (g->copy_start) cudaEventDestroy(g->copy_start);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     cudaFree(g->d_q);
     cudaFree(g->d_s);
     cudaFree(g->d_p);
@@ -480,9 +483,11 @@ static tnlm_status sweep_t(const KGeom &kg, const __half *wsrc, const __half *va
 // the residual and every sum stay FP32.
 // Step 1 of an FBS iteration k, (P1) from f^(k-1) into g: CGLS (the paper's solver) or n_inner
 // gradient steps.  report: the residual norms go to the handle's scalars (slots of iteration k).
+// phase_ready (FP32 gradient steps only): one event per phase, recorded when that phase of f and its views
+// of y are in place; the first projection then starts phase by phase as the events complete.
 template <class T>
 static tnlm_status p1_step(tnlm_geometry *geo, const T *y, const T *f, T *g, const tnlm_params *p, int k,
-                           bool report, StageTimer *timer, cudaStream_t st)
+                           bool report, StageTimer *timer, cudaStream_t st, const cudaEvent_t *phase_ready = nullptr)
 {
     const KGeom &kg = geo->kg;
     const long long nblk = forward_blocks(kg, geo->n_views_total);
@@ -499,7 +504,19 @@ static tnlm_status p1_step(tnlm_geometry *geo, const T *y, const T *f, T *g, con
     for (int t = 0; t < (p->p1_solver == 1 ? 0 : p->n_inner); ++t) {
         const T *src = t == 0 ? f : g;
         if (timer) timer->begin(0);
-        TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
+        if constexpr (std::is_same<T, float>::value) {
+            if (t == 0 && phase_ready) {
+                for (int ph = 0; ph < kg.np; ++ph) {
+                    TNLM_TRY_CUDA(cudaStreamWaitEvent(st, phase_ready[ph], 0));
+                    TNLM_TRY(launch_forward_phase(kg, geo->d_views, ph, geo->view_off[ph], geo->view_off[ph + 1], src,
+                                                  y, geo->d_r, geo->d_part, st));
+                }
+            } else {
+                TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
+            }
+        } else {
+            TNLM_TRY(launch_forward(kg, geo->d_views, geo->n_views_total, src, y, geo->d_r, geo->d_part, 1, st));
+        }
         if (timer) timer->end();
         if (report) TNLM_TRY(launch_sum_partials(geo->d_part, nblk, geo->d_scalars + (long long)k * p->n_inner + t, st));
         if (timer) timer->begin(1);
@@ -512,11 +529,11 @@ static tnlm_status p1_step(tnlm_geometry *geo, const T *y, const T *f, T *g, con
 
 template <class T>
 static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, int k, bool report,
-                                 StageTimer *timer, cudaStream_t st)
+                                 StageTimer *timer, cudaStream_t st, const cudaEvent_t *phase_ready = nullptr)
 {
     const KGeom &kg = geo->kg;
     T *g = reinterpret_cast<T *>(geo->d_g), *tmp = reinterpret_cast<T *>(geo->d_tmp);
-    TNLM_TRY(p1_step<T>(geo, y, f, g, p, k, report, timer, st));
+    TNLM_TRY(p1_step<T>(geo, y, f, g, p, k, report, timer, st, phase_ready));
     // steps 2-4: weights from g^(k) fused into the Eq. 8 sweep(s), positivity after the last
     if (timer) timer->begin(2);
     const int ngj = p->n_gj > 0 ? p->n_gj : 1;
@@ -536,17 +553,11 @@ static tnlm_status fbs_iteration(tnlm_geometry *geo, const T *y, T *f, const tnl
 
 }  // namespace tnlm
 
-template <class T>
-static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, double *report,
-                                 void *stream)
+// The residual norms of a run into the caller's report (synchronises st).
+static tnlm_status copy_report(tnlm_geometry *geo, const tnlm_params *p, double *report, cudaStream_t st)
 {
-    if (!p) return arg_error("params must not be NULL");
     const long long n_norms = (long long)p->n_outer * p->n_inner;
-    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
-    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots, !std::is_same<T, float>::value));
-    cudaStream_t st = as_stream(stream);
-    StageTimer timer(geo, st);
-    for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration<T>(geo, y, f, p, k, report != nullptr, &timer, st));
+    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);
     if (report && n_norms > 0) {
         if (p->p1_solver == 1) {  // keep the residual before each of the n_inner CGLS iterations
             std::vector<double> tmp((size_t)n_slots);
@@ -559,7 +570,34 @@ static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnl
             TNLM_TRY_CUDA(cudaStreamSynchronize(st));
         }
     }
+    return TNLM_OK;
+}
+
+template <class T>
+static tnlm_status reconstruct_t(tnlm_geometry *geo, const T *y, T *f, const tnlm_params *p, double *report,
+                                 void *stream)
+{
+    if (!p) return arg_error("params must not be NULL");
+    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);  // CGLS reports n_inner + 1 per iteration
+    TNLM_TRY(prepare_reconstruct(geo, y, f, p, n_slots, !std::is_same<T, float>::value));
+    cudaStream_t st = as_stream(stream);
+    StageTimer timer(geo, st);
+    for (int k = 0; k < p->n_outer; ++k) TNLM_TRY(fbs_iteration<T>(geo, y, f, p, k, report != nullptr, &timer, st));
+    TNLM_TRY(copy_report(geo, p, report, st));
     return timer.finish();
+}
+
+// The handle's copy stream and per-phase events for the host-buffer entry point.
+static tnlm_status ensure_copy_events(tnlm_geometry *geo)
+{
+    if (!geo->copy_stream) TNLM_TRY_CUDA(cudaStreamCreateWithFlags(&geo->copy_stream, cudaStreamNonBlocking));
+    if (!geo->copy_start) TNLM_TRY_CUDA(cudaEventCreateWithFlags(&geo->copy_start, cudaEventDisableTiming));
+    while ((int)geo->phase_ready.size() < geo->kg.np) {
+        cudaEvent_t e = nullptr;
+        TNLM_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        geo->phase_ready.push_back(e);
+    }
+    return TNLM_OK;
 }
 
 extern "C" {
@@ -568,6 +606,41 @@ tnlm_status tnlm_reconstruct(tnlm_geometry *geo, const float *y, float *f, const
                              void *stream)
 {
     return reconstruct_t<float>(geo, y, f, p, report, stream);
+}
+
+tnlm_status tnlm_reconstruct_host(tnlm_geometry *geo, const float *y_host, float *f_host, float *y_dev, float *f_dev,
+                                  const tnlm_params *p, double *report, void *stream)
+{
+    if (!geo || !y_host || !f_host || !y_dev || !f_dev)
+        return arg_error("geometry, y_host, f_host, y_dev and f_dev must not be NULL");
+    if (!p) return arg_error("params must not be NULL");
+    const long long n_slots = (long long)p->n_outer * (p->n_inner + 1);
+    TNLM_TRY(prepare_reconstruct(geo, y_dev, f_dev, p, n_slots, false));
+    TNLM_TRY(ensure_copy_events(geo));
+    cudaStream_t st = as_stream(stream);
+    const KGeom &kg = geo->kg;
+    // the copies overwrite y_dev and f_dev only after the work queued on st before this call
+    TNLM_TRY_CUDA(cudaEventRecord(geo->copy_start, st));
+    TNLM_TRY_CUDA(cudaStreamWaitEvent(geo->copy_stream, geo->copy_start, 0));
+    for (int ph = 0; ph < kg.np; ++ph) {
+        const long long v0 = geo->view_off[ph], nv = geo->view_off[ph + 1] - v0;
+        TNLM_TRY_CUDA(cudaMemcpyAsync(f_dev + (long long)ph * kg.nvox, f_host + (long long)ph * kg.nvox,
+                                      sizeof(float) * kg.nvox, cudaMemcpyHostToDevice, geo->copy_stream));
+        TNLM_TRY_CUDA(cudaMemcpyAsync(y_dev + v0 * kg.npix, y_host + v0 * kg.npix, sizeof(float) * nv * kg.npix,
+                                      cudaMemcpyHostToDevice, geo->copy_stream));
+        TNLM_TRY_CUDA(cudaEventRecord(geo->phase_ready[ph], geo->copy_stream));
+    }
+    // with gradient steps the first projection starts phase by phase as the copies land
+    const bool pipelined = p->p1_solver == 0 && p->n_outer > 0 && p->n_inner > 0;
+    if (!pipelined)
+        for (int ph = 0; ph < kg.np; ++ph) TNLM_TRY_CUDA(cudaStreamWaitEvent(st, geo->phase_ready[ph], 0));
+    StageTimer timer(geo, st);
+    for (int k = 0; k < p->n_outer; ++k)
+        TNLM_TRY(fbs_iteration<float>(geo, y_dev, f_dev, p, k, report != nullptr, &timer, st,
+                                      k == 0 && pipelined ? geo->phase_ready.data() : nullptr));
+    TNLM_TRY_CUDA(cudaMemcpyAsync(f_host, f_dev, sizeof(float) * kg.np * kg.nvox, cudaMemcpyDeviceToHost, st));
+    TNLM_TRY(copy_report(geo, p, report, st));
+    return timer.finish();
 }
 
 tnlm_status tnlm_reconstruct_bf16(tnlm_geometry *geo, const uint16_t *y, uint16_t *f, const tnlm_params *p,

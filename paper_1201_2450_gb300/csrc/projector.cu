@@ -586,6 +586,54 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
     return launch_forward_t<float>(kg, views, n_views_total, vol, y, out, partials, mode, st);
 }
 
+// One phase's share of a mode-1 projection: phase ph of vol is bricked (table walker) and views
+// [view_lo, view_hi) projected, writing the same rows of out and the same block partials as the
+// whole-volume launch does; the phases of a volume may so be projected as they arrive.
+template <int BY>
+static void launch_phase_by(const KGeom &kg, const ViewGeom *views, int ph, int view_lo, int view_hi, const float *vol,
+                            const float *y, float *out, double *partials, bool tab, cudaStream_t st)
+{
+    const int n = view_hi - view_lo;
+    const long long off = (long long)view_lo * kg.npix;
+    double *part = partials + (long long)view_lo * ((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + BY - 1) / BY);
+    dim3 grid((kg.nu + kFwdBX - 1) / kFwdBX, (kg.nv + BY - 1) / BY, n);
+    if (tab) {
+        float *volb = static_cast<float *>(kg.volb);
+        KGeom kb = kg;
+        kb.np = 1;
+        const long long nt = (long long)((kg.nx + 3) / 4) * ((kg.ny + 1) / 2) * kg.nz;
+        const long long nb = (nt + 255) / 256;
+        k_brick<float><<<(unsigned)(nb < 152 * 64 ? nb : 152 * 64), 256, 0, st>>>(
+            kb, vol + (long long)ph * kg.nvox, volb + (long long)ph * kg.nz * kg.brick_slice);
+        KGeom kt = kg;
+        kt.coltab = kg.coltab + (long long)view_lo * kg.coltab_kmax * kg.nu;
+        k_forward_tab<1, BY, float><<<grid, dim3(kFwdBX, BY), 0, st>>>(kt, views + view_lo, volb, y + off, out + off,
+                                                                         part);
+    } else {
+        k_forward<1, BY, float><<<grid, dim3(kFwdBX, BY), 0, st>>>(kg, views + view_lo, vol, y + off, out + off, part);
+    }
+}
+
+tnlm_status launch_forward_phase(const KGeom &kg, const ViewGeom *views, int ph, int view_lo, int view_hi,
+                                 const float *vol, const float *y, float *out, double *partials, cudaStream_t st)
+{
+    if (!forward_shape_valid(kg.fwd_by)) {
+        set_error("projector launch shape must be 2, 4, 8 (slab walker) or 102, 104, 108 (table walker) (got %d)",
+                  kg.fwd_by);
+        return TNLM_ERR_ARG;
+    }
+    if (view_hi <= view_lo) return TNLM_OK;
+    const int code = forward_shape_in_use(kg);
+    const bool tab = code > 100;
+    switch (code % 100) {
+    case 2: launch_phase_by<2>(kg, views, ph, view_lo, view_hi, vol, y, out, partials, tab, st); break;
+    case 8: launch_phase_by<8>(kg, views, ph, view_lo, view_hi, vol, y, out, partials, tab, st); break;
+    default: launch_phase_by<4>(kg, views, ph, view_lo, view_hi, vol, y, out, partials, tab, st); break;
+    }
+    TNLM_TRY_CUDA(cudaGetLastError());
+    return TNLM_OK;
+}
+
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const uint16_t *vol,
                            const uint16_t *y, float *out, double *partials, int mode, cudaStream_t st)
 {

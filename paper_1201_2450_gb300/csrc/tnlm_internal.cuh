@@ -75,6 +75,10 @@ tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_t
 // FP16 storage of vol and y, FP32 arithmetic and FP32 output
 tnlm_status launch_forward(const KGeom &kg, const ViewGeom *views, int n_views_total, const __half *vol,
                            const __half *y, float *out, double *partials, int mode, cudaStream_t st);
+// Phase ph's share of a mode-1 FP32 projection (its views [view_lo, view_hi)): the same rows of out and
+// block partials as launch_forward writes for them.
+tnlm_status launch_forward_phase(const KGeom &kg, const ViewGeom *views, int ph, int view_lo, int view_hi,
+                                 const float *vol, const float *y, float *out, double *partials, cudaStream_t st);
 long long forward_blocks(const KGeom &kg, int n_views_total);
 long long forward_blocks_max(const KGeom &kg, int n_views_total);  // over every projector block shape
 bool forward_shape_valid(int code);  // projector launch shape code (KGeom::fwd_by)
@@ -267,6 +271,10 @@ struct tnlm_geometry {
     float *d_pref = nullptr;          // column prefix sums for the transpose (prefix_floats)
     float2 *d_coltab = nullptr;       // column tables of the table projector (coltab_entries)
     void *d_volb = nullptr;           // its bricked volume copy (brick_bytes)
+    // host-buffer entry point: a copy stream and one event per phase (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_start = nullptr;
+    std::vector<cudaEvent_t> phase_ready;
     bool coltab_failed = false;       // their allocation failed once: the slab walker runs
     // CGLS workspace (allocated on first use)
     float *d_q = nullptr;             // sum(n_views) * npix

@@ -112,6 +112,9 @@ def test_launch_shape_setters_reject_uncompiled_shapes(lib):
     assert lib.tnlm_set_sweep_shape(5, 3, 0, 0) == 1
     lib.tnlm_set_launch_shapes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
     assert lib.tnlm_set_launch_shapes(None, 4, 8, 4) == 1
+    lib.tnlm_reconstruct_host.argtypes = [C.c_void_p] * 8
+    assert lib.tnlm_reconstruct_host(None, None, None, None, None, None, None, None) == 1
+    assert b"must not be NULL" in lib.tnlm_last_error()
     lib.tnlm_get_launch_shapes.argtypes = [C.c_void_p, C.c_void_p]
     out = (C.c_int * 3)()
     assert lib.tnlm_get_launch_shapes(None, out) == 1

@@ -369,6 +369,27 @@ def test_full_size_sweep_sampled_voxels(ora, c2_full):
     assert rel_l2(got, ref) <= RTOL
 
 
+def test_sweep_far_beyond_rescale_threshold(ora):
+    """Uniform data with h = 0.02 puts c2 D near 10^4: the running references of the online
+    normalisation move by far more than the rescale threshold, and no warp skips the rescale
+    test.  A volume large enough for interior and boundary tiles of every launch shape; sampled
+    voxels (corners, faces and the middle) against the oracle."""
+    shape = (3, 24, 40, 72)
+    a = synth.uniform(shape, 900)
+    v = synth.uniform(shape, 901)
+    g = synth.uniform(shape, 902)
+    d, M, h, mu = 1, 3, 0.02, 0.8
+    out = tnlm.tnlm_gauss_jacobi(cuda(a), cuda(v), cuda(g), d, M, h, mu, 0).cpu().numpy()
+    assert np.isfinite(out).all()
+    rng = np.random.default_rng(903)
+    pts = [(int(rng.integers(3)), int(rng.integers(24)), int(rng.integers(40)), int(rng.integers(72)))
+           for _ in range(150)]
+    pts += [(0, 0, 0, 0), (1, 23, 39, 71), (2, 12, 20, 36), (1, 0, 20, 71), (2, 23, 0, 36)]
+    got = np.array([out[ph, z, yy, xx] for ph, z, yy, xx in pts])
+    ref = np.array([ora.gj_voxel(a, v, g, ph, xx, yy, z, d, M, h, mu, 0) for ph, z, yy, xx in pts])
+    assert rel_l2(got, ref) <= RTOL
+
+
 @pytest.fixture(scope="module")
 def c3_full():
     g, _ = synth.enhance_input(synth.C3, device="cuda")
@@ -1082,3 +1103,32 @@ def test_grouped_persistent_sweep_equals_per_problem_plan(ora):
     pb, p = probs[1], params[1]
     ref = ora.reconstruct(ora.Geometry(pb.geom), pb.y.numpy(), np.zeros(Gs[1].vol_shape), p.tau, 1, 3, 0.02, 1.0, 3)
     assert rel_l2(f_group[1].cpu().numpy(), ref) <= RTOL
+
+
+@pytest.mark.parametrize("name, shape", [("ragged_uneven", 104), ("ragged_uneven", 4), ("c1", 104)])
+def test_reconstruct_host_equals_device_call(name, shape):
+    """tnlm_reconstruct_host (phase-by-phase copies from pinned host memory, the first projection
+    started per phase as its copy lands) against tnlm_reconstruct on the same inputs: f and the
+    residual report bit for bit, with the table and the slab walker; CGLS (no per-phase start) and
+    n_outer = 0 (f copied there and back)."""
+    G = tnlm.Geometry(GEOMS[name])
+    tnlm.tnlm_set_launch_shapes(G, shape, 8, 4)
+    y = synth.uniform(G.proj_shape, 880) * 0.3
+    f0 = synth.smooth_volume(G.vol_shape, 881)
+    L = tnlm.tnlm_operator_norm(G, cuda(synth.uniform(G.vol_shape, 882)), 20)
+    cases = [tnlm.Params(d=1, M=2, h=0.02, mu=0.7, tau=1.0 / L, n_outer=2, n_inner=2, clip_nonneg=1),
+             tnlm.Params(d=1, M=2, h=0.02, mu=0.7, n_outer=1, n_inner=2, p1_solver=1),
+             tnlm.Params(d=1, M=2, h=0.02, mu=0.7, tau=1.0 / L, n_outer=0)]
+    for p in cases:
+        f_dev_ref = cuda(f0)
+        _, rep_ref = tnlm.tnlm_reconstruct(G, cuda(y), f_dev_ref, p, report=True)
+        y_host = torch.from_numpy(np.ascontiguousarray(y, np.float32)).pin_memory()
+        f_host = torch.from_numpy(np.ascontiguousarray(f0, np.float32)).pin_memory()
+        y_dev = torch.full(G.proj_shape, float("nan"), device="cuda")
+        f_dev = torch.full(G.vol_shape, float("nan"), device="cuda")
+        *_, rep = tnlm.reconstruct_host(G, y_host, f_host, p, y_dev, f_dev, report=True)
+        torch.cuda.synchronize()
+        assert torch.equal(f_host, f_dev_ref.cpu())
+        assert torch.equal(f_dev, f_dev_ref)
+        assert np.array_equal(rep, rep_ref)
+    G.close()
