@@ -394,8 +394,9 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * many detector pixels, one ray per thread, each ray finding all its own
  * crossings) or 102, 104 or 108 (the table walker: blocks of 32 x 2, 4 or 8
  * pixels; the xy cells every detector column crosses are laid out once per
- * handle in device memory, views x (nx + ny + 2) x nu entries of 8 bytes,
- * and each ray adds only its own z crossings, reading a copy of the volume
+ * handle in device memory, views x (nx + ny + 2, rounded up to even) x nu
+ * entries of 8 bytes, and each ray adds only its own z crossings, reading a
+ * copy of the volume
  * that each projection first writes into the handle's workspace with its
  * z slices in 4 x 8 (x, y) bricks: N_p x nz x ceil(nx/4) x ceil(ny/8) x 32
  * voxels of 4 bytes).  A new handle starts at 104; its tables are built,

@@ -183,6 +183,13 @@ __global__ void __launch_bounds__(kFwdBX *BY)
 
 constexpr int kColtabPad = 3;  // exit entry repeated after the last so reads ahead need no test
 
+// Entries of one (view, column) are stored in pairs: pair j of column iu of view vg holds entries 2j, 2j+1 as
+// one float4 at float4 index (vg * kmax / 2 + j) * nu + iu (kmax even), so a warp's lanes read adjacent pairs.
+__host__ __device__ __forceinline__ long long coltab_slot(int vg, int e, int iu, int kmax, int nu)
+{
+    return (((long long)vg * (kmax >> 1) + (e >> 1)) * nu + iu) * 2 + (e & 1);
+}
+
 // The in-plane part of the ray of detector column iu of view V, shared by
 // k_coltab and k_forward_tab (the same expressions as k_forward).
 struct ColumnRay {
@@ -254,7 +261,8 @@ struct ColumnRay {
 // order, found by binary search over the other axis (ties: the a-plane first);
 // the thread with t == n_a + n_b writes the exit, and repeats it in the next
 // kColtabPad slots so that the walk can read ahead without bounds tests.
-// Layout: tab[(vg * kmax + k) * nu + iu], kmax = nx + ny - 1 + kColtabPad.
+// Layout: pairs of entries interleaved by column (coltab_slot), kmax = nx + ny - 1 + kColtabPad rounded up to
+// an even count.
 __global__ void __launch_bounds__(128) k_coltab(KGeom G, const ViewGeom *__restrict__ views, float2 *__restrict__ tab,
                                                 int kmax)
 {
@@ -299,9 +307,9 @@ __global__ void __launch_bounds__(128) k_coltab(KGeom G, const ViewGeom *__restr
     }
     // the cell before this crossing; the crossing clamped to the column's extent
     const float2 ent = make_float2(fminf(fmaxf(beta, R.blo), R.bhi), __int_as_float(R.cell(ca, cb, (G.nx + 3) >> 2)));
-    tab[((long long)vg * kmax + e) * G.nu + iu] = ent;
+    tab[coltab_slot(vg, e, iu, kmax, G.nu)] = ent;
     if (t == R.n_a + R.n_b)
-        for (int q = 1; q <= kColtabPad; ++q) tab[((long long)vg * kmax + e + q) * G.nu + iu] = ent;
+        for (int q = 1; q <= kColtabPad; ++q) tab[coltab_slot(vg, e + q, iu, kmax, G.nu)] = ent;
 }
 
 
@@ -342,8 +350,9 @@ __global__ void __launch_bounds__(kFwdBX *BY)
             float bc = nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
             const long long zstep = sc * G.brick_slice;  // vol: the bricked copy
             const T *__restrict__ fp = vol + ((long long)V.phase * G.nz + ic0) * G.brick_slice;
-            const long long st = G.nu;  // entry stride in the interleaved tables
-            const float2 *__restrict__ tc = G.coltab + (long long)vg * G.coltab_kmax * st + iu;
+            const long long st = G.nu;  // pair stride in the interleaved tables
+            const float2 *__restrict__ tc = G.coltab + coltab_slot(vg, 0, iu, G.coltab_kmax, G.nu);
+            auto entry_x = [&](int e) { return __ldg(tc + (long long)(e >> 1) * 2 * st + (e & 1)).x; };
             const int K = R.entries();
             // this row's entries: the first that ends after blo .. the first that ends at or after bhi
             // (rows inside the volume's z range enter and leave through its sides: all entries)
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                 int lo = 0, hi = K - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (__ldg(tc + mid * st).x > blo) hi = mid;
+                    if (entry_x(mid) > blo) hi = mid;
                     else lo = mid + 1;
                 }
                 k0 = lo;
@@ -361,64 +370,75 @@ __global__ void __launch_bounds__(kFwdBX *BY)
                 int lo = k0, hi = K - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (__ldg(tc + mid * st).x >= bhi) hi = mid;
+                    if (entry_x(mid) >= bhi) hi = mid;
                     else lo = mid + 1;
                 }
                 k1 = lo;
             }
             float bcur = blo;
-            const float2 *__restrict__ tp = tc + k0 * st;
-            float2 t0 = __ldg(tp), t1 = __ldg(tp + st);
-            // entries before k1 end before bhi (the tables ascend), so only the last entry is clamped
-            // to the row's exit: pairs of entries strictly before k1 first, then the last one or two
+            // one table entry (end e, cell offset c): its z crossings, then the rest of its segment
+            auto segment = [&](float e, float c) {
+                float f = ldg_v(fp + __float_as_int(c));
+                while (bc < e) {
+                    acc = fmaf(f, bc - bcur, acc);
+                    bcur = bc;
+                    fp += zstep;
+                    f = ldg_v(fp + __float_as_int(c));
+                    fc += scf;
+                    bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
+                }
+                acc = fmaf(f, e - bcur, acc);
+                bcur = e;
+            };
+            // entries before k1 end before bhi (the tables ascend), so only the last entry is clamped to
+            // the row's exit
+            const float4 *__restrict__ tp = reinterpret_cast<const float4 *>(tc) + (long long)(k0 >> 1) * st;
+            float4 t = __ldg(tp);
             int k = k0;
-            for (; k + 1 < k1; k += 2) {
-                tp += 2 * st;
-                const float2 n0 = __ldg(tp), n1 = __ldg(tp + st);  // entries k+2, k+3 (at most k1 + 1)
-                float f0 = ldg_v(fp + __float_as_int(t0.y));
-                float f1 = ldg_v(fp + __float_as_int(t1.y));
-                float e = t0.x;
+            if ((k & 1) && k < k1) {  // the first entry is the second of its pair
+                segment(t.z, t.w);
+                ++k;
+                tp += st;
+                t = __ldg(tp);
+            }
+            for (; k + 1 < k1; k += 2) {  // pairs of entries strictly before k1, the next pair in flight
+                tp += st;
+                const float4 n = __ldg(tp);
+                float f0 = ldg_v(fp + __float_as_int(t.y));
+                float f1 = ldg_v(fp + __float_as_int(t.w));
+                float e = t.x;
                 if (bc < e) {
                     do {  // z crossings inside entry k's segment
                         acc = fmaf(f0, bc - bcur, acc);
                         bcur = bc;
                         fp += zstep;
-                        f0 = ldg_v(fp + __float_as_int(t0.y));
+                        f0 = ldg_v(fp + __float_as_int(t.y));
                         fc += scf;
                         bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
                     } while (bc < e);
-                    f1 = ldg_v(fp + __float_as_int(t1.y));
+                    f1 = ldg_v(fp + __float_as_int(t.w));
                 }
                 acc = fmaf(f0, e - bcur, acc);
                 bcur = e;
-                e = t1.x;
+                e = t.z;
                 while (bc < e) {  // z crossings inside entry k+1's segment
                     acc = fmaf(f1, bc - bcur, acc);
                     bcur = bc;
                     fp += zstep;
-                    f1 = ldg_v(fp + __float_as_int(t1.y));
+                    f1 = ldg_v(fp + __float_as_int(t.w));
                     fc += scf;
                     bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
                 }
                 acc = fmaf(f1, e - bcur, acc);
                 bcur = e;
-                t0 = n0;
-                t1 = n1;
+                t = n;
             }
-            for (; k <= k1; ++k) {  // entries k1 - 1 (if not taken above) and k1
-                float f0 = ldg_v(fp + __float_as_int(t0.y));
-                const float e = fminf(t0.x, bhi);
-                while (bc < e) {
-                    acc = fmaf(f0, bc - bcur, acc);
-                    bcur = bc;
-                    fp += zstep;
-                    f0 = ldg_v(fp + __float_as_int(t0.y));
-                    fc += scf;
-                    bc = --nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
-                }
-                acc = fmaf(f0, e - bcur, acc);
-                bcur = e;
-                t0 = t1;
+            // the last one or two entries: k1 alone (k odd), or k (even) and then k1 if k < k1
+            if (k & 1) {
+                segment(fminf(t.z, bhi), t.w);
+            } else {
+                segment(fminf(t.x, bhi), t.y);
+                if (k < k1) segment(fminf(t.z, bhi), t.w);
             }
         }
         const float pf = acc * len;
@@ -511,7 +531,7 @@ long long forward_blocks_max(const KGeom &kg, int n_views_total)
     return (long long)((kg.nu + kFwdBX - 1) / kFwdBX) * ((kg.nv + 1) / 2) * n_views_total;  // fewest rows: 2
 }
 
-int coltab_kmax(const KGeom &kg) { return kg.nx + kg.ny - 1 + kColtabPad; }
+int coltab_kmax(const KGeom &kg) { return (kg.nx + kg.ny - 1 + kColtabPad + 1) & ~1; }
 
 size_t coltab_entries(const KGeom &kg, int n_views_total)
 {
