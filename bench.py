@@ -46,10 +46,10 @@ WORKLOAD = ("NCAT-shaped 4D TNLM-R FP32: 10 phases x 256x256x64 @ 2 mm, 36 views
 # each kernel on this workload, with the SHA-256 of the kernel source it was
 # measured on; a changed source invalidates the figure (reported as null).
 NCU_TRAFFIC = {
-    # 6-phase captures (profiles/k_*_ncat_6x256x256x64.md) scaled by 10/6 to the 10-phase workload; the
+    # single-kernel captures on the 6-phase case of this workload, scaled by 10/6 to its 10 phases; the
     # projector stage is the bricked copy plus the table walk, the transpose stage the column scan plus the bands
-    "k_forward": {"bytes_per_launch": int((100.750848e6 + 48.628480e6 + 592.987392e6 + 162.353920e6) * 10 / 6),
-                  "source_sha": "4d2e1dace0dc409b"},
+    "k_forward": {"bytes_per_launch": int((100.766720e6 + 48.687104e6 + 591.842048e6 + 162.420736e6) * 10 / 6),
+                  "source_sha": "3a0488208b82ccb9"},
     "k_backproject": {"bytes_per_launch": int((169.919488e6 + 284.322560e6 + 556.931328e6 + 93.128448e6) * 10 / 6),
                       "source_sha": "5aa935fcb93c583b"},
     "k_sweep": {"bytes_per_launch": int((162.544640e6 + 83.844608e6) * 10 / 6), "source_sha": "aa475743b3412a05"},
