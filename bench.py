@@ -180,12 +180,14 @@ K1_FLOP_SLAB, K1_FLOP_B, K1_FLOP_C = 12, 3, 7
 # (its segment length and FMA, the next z plane by an add and one FMA); so per ray
 # 4 (1 + |dx| + |dy|) + 6 |dz|.  The tables themselves are built once per geometry, not per launch.
 K1_TAB_FLOP_ENTRY, K1_TAB_FLOP_C = 4, 6
-# FP32 operations of the band transpose per non-zero of P, counted from its source on this geometry:
-# per (column of 8 cells, view, pixel column) about 46 for the chord and row maps and 26 per cell
-# boundary (its row images, the band row split, the full-row prefix difference), 280 in all, plus
-# ~13 for the column's footprint per view shared by its ~3.5 pixel columns, over the ~38 (ray,
-# cell) pairs that chord serves (about 4.8 detector rows per 2 mm cell).
-K2_FLOP_PER_NNZ = 7.7
+# FP32 operations of the band transpose per non-zero of P, counted from its source on this geometry
+# (an FMA counts 2, a min/max or a conversion 1): per (column of 8 cells, view, pixel column) 38 for
+# the chord (two slab tests) and the row-map slopes, 12 for the chord midpoint, the first boundary
+# and its row images, then 30 per cell boundary (the boundary height, its two row images with their
+# margins, the band row's split and its two accumulations, the prefix difference of the full rows),
+# 320 in all, plus ~13 for the column's footprint per view shared by its ~3.5 pixel columns, over
+# the ~38 (ray, cell) pairs that chord serves (about 4.8 detector rows per 2 mm cell).
+K2_FLOP_PER_NNZ = 8.5
 
 
 def projection_counts(desc: dict, device="cuda") -> tuple[int, int, int]:
