@@ -176,10 +176,10 @@ def projection_nnz(desc: dict, device="cuda") -> int:
 # z plane); so per ray 12 (1 + |da|) + 3 |db| + 7 |dc| with da, db, dc the cell steps along each axis.
 K1_FLOP_SLAB, K1_FLOP_B, K1_FLOP_C = 12, 3, 7
 # FP32 operations of the table walk (the default projector), counted from its source: per xy-table
-# entry 4 (the entry's end clamped to the ray's exit, its segment length and FMA), per z crossing 6
-# (its segment length and FMA, the next z plane by an add and one FMA); so per ray
-# 4 (1 + |dx| + |dy|) + 6 |dz|.  The tables themselves are built once per geometry, not per launch.
-K1_TAB_FLOP_ENTRY, K1_TAB_FLOP_C = 4, 6
+# entry 3 (its segment length and FMA; only a row's last entry is clamped to its exit), per z crossing
+# 6 (its segment length and FMA, the next z plane by an add and one FMA); so per ray
+# 3 (1 + |dx| + |dy|) + 6 |dz|.  The tables themselves are built once per geometry, not per launch.
+K1_TAB_FLOP_ENTRY, K1_TAB_FLOP_C = 3, 6
 # FP32 operations of the band transpose per non-zero of P, counted from its source on this geometry
 # (an FMA counts 2, a min/max or a conversion 1): per (column of 8 cells, view, pixel column) 38 for
 # the chord (two slab tests) and the row-map slopes, 12 for the chord midpoint, the first boundary
