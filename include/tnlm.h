@@ -399,7 +399,7 @@ tnlm_status tnlm_energy_grad_weights(int nx, int ny, int nz, int n_phases, const
  * copy of the volume
  * that each projection first writes into the handle's workspace with its
  * z slices in 4 x 8 (x, y) bricks: N_p x nz x ceil(nx/4) x ceil(ny/8) x 32
- * voxels of 4 bytes).  A new handle starts at 104; its tables are built,
+ * voxels of 4 bytes, FP32 also for 16-bit storage).  A new handle starts at 104; its tables are built,
  * synchronising the device, by the first call that projects (or by
  * tnlm_set_launch_shapes), never during a stream capture; if the tables or
  * the copy cannot be allocated the slab walker with 4 rows runs.  The two

@@ -320,9 +320,10 @@ __global__ void __launch_bounds__(128) k_coltab(KGeom G, const ViewGeom *__restr
 // applies).
 // Launch bounds: 64 warps per SM (the walk is latency-bound on its voxel gathers, and full occupancy at 32
 // registers, with a few bytes spilled, beats 48 warps at 40 registers by 5 %).
+// vol: the bricked FP32 copy (widened from 16-bit storage by k_brick); y: the stored measurements.
 template <int MODE, int BY, class T>
 __global__ void __launch_bounds__(kFwdBX *BY, 64 / BY)
-    k_forward_tab(KGeom G, const ViewGeom *__restrict__ views, const T *__restrict__ vol,
+    k_forward_tab(KGeom G, const ViewGeom *__restrict__ views, const float *__restrict__ vol,
                   const T *__restrict__ y, float *__restrict__ out, double *__restrict__ partials)
 {
     __shared__ double ws[BY];
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(kFwdBX *BY, 64 / BY)
             float fc = (float)(ic0 + (Gz > 0.f));
             float bc = nzc > 0 ? fmaf(fc, ivc, oc) : FLT_MAX;
             const long long zstep = sc * G.brick_slice;  // vol: the bricked copy
-            const T *__restrict__ fp = vol + ((long long)V.phase * G.nz + ic0) * G.brick_slice;
+            const float *__restrict__ fp = vol + ((long long)V.phase * G.nz + ic0) * G.brick_slice;
             const long long st = G.nu;  // pair stride in the interleaved tables
             const float2 *__restrict__ tc = G.coltab + coltab_slot(vg, 0, iu, G.coltab_kmax, G.nu);
             auto entry_x = [&](int e) { return __ldg(tc + (long long)(e >> 1) * 2 * st + (e & 1)).x; };
@@ -463,10 +464,11 @@ __global__ void __launch_bounds__(kFwdBX *BY, 64 / BY)
 // The bricked copy of the volume: thread t of z slice (phase, z) takes the
 // 4 x 2 voxels x = 4 bx .. 4 bx + 3, y = 2 py, 2 py + 1 and writes them as the
 // 8 consecutive elements they occupy in brick (bx, py / 4) (rows 2 py and
-// 2 py + 1 of a brick are adjacent).  Elements outside the volume are
-// written as 0 and never read.
+// 2 py + 1 of a brick are adjacent), in FP32 whatever the stored type (16-bit
+// values are widened once here rather than at every gather of the walk).
+// Elements outside the volume are written as 0 and never read.
 template <class T>
-__global__ void __launch_bounds__(256) k_brick(KGeom G, const T *__restrict__ vol, T *__restrict__ volb)
+__global__ void __launch_bounds__(256) k_brick(KGeom G, const T *__restrict__ vol, float *__restrict__ volb)
 {
     const int nxb = (G.nx + 3) >> 2, nyh = (G.ny + 1) >> 1;
     const long long per_slice = (long long)nxb * nyh;
@@ -477,29 +479,17 @@ __global__ void __launch_bounds__(256) k_brick(KGeom G, const T *__restrict__ vo
         const int r = (int)(t - sl * per_slice);
         const int bx = r % nxb, py = r / nxb;
         const T *src = vol + sl * G.nx * G.ny;
-        T v[8];
+        float v[8];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int x = 4 * bx + i, y = 2 * py + j;
-                v[4 * j + i] = (x < G.nx && y < G.ny) ? src[(long long)y * G.nx + x] : T(0.f);
+                v[4 * j + i] = (x < G.nx && y < G.ny) ? ld_v(src + (long long)y * G.nx + x) : 0.f;
             }
-        T *dst = volb + sl * G.brick_slice + ((((long long)(py >> 2) * nxb + bx) << 5) + ((py & 3) << 3));
-        if constexpr (sizeof(T) == 4) {
-            reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-            reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-        } else {
-            uint4 w;
-            unsigned short h[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) h[k] = *reinterpret_cast<const unsigned short *>(&v[k]);
-            w.x = h[0] | ((unsigned)h[1] << 16);
-            w.y = h[2] | ((unsigned)h[3] << 16);
-            w.z = h[4] | ((unsigned)h[5] << 16);
-            w.w = h[6] | ((unsigned)h[7] << 16);
-            *reinterpret_cast<uint4 *>(dst) = w;
-        }
+        float *dst = volb + sl * G.brick_slice + ((((long long)(py >> 2) * nxb + bx) << 5) + ((py & 3) << 3));
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
     }
 }
 
@@ -565,7 +555,7 @@ template <int MODE, int BY, class T>
 static void launch_forward_tab(const KGeom &kg, const ViewGeom *views, int n_views_total, const T *vol, const T *y,
                                float *out, double *partials, cudaStream_t st)
 {
-    T *volb = static_cast<T *>(kg.volb);
+    float *volb = static_cast<float *>(kg.volb);
     const long long n = (long long)((kg.nx + 3) / 4) * ((kg.ny + 1) / 2) * kg.nz * kg.np;
     const long long nb = (n + 255) / 256;
     k_brick<T><<<(unsigned)(nb < 152 * 64 ? nb : 152 * 64), 256, 0, st>>>(kg, vol, volb);
